@@ -1,0 +1,208 @@
+/*
+ * Oracle for the batched Kronecker product action -- TEST INFRASTRUCTURE ONLY.
+ *
+ * Plain, slow, obviously correct CPU loops.  Only the tests, the smoke check and
+ * the CPU-baseline leg of the benchmark may call this file; the product path
+ * never does.  It shares no code, header or constant with the CUDA library.
+ *
+ * Conventions (paper Sec. 2 and Sec. 2.1, with the factor order written as
+ * (A (x) B) vec(X) = vec(B X A^T), the last Kronecker factor acting on the
+ * fastest, column-major mode):
+ *
+ *   2-D:  Y^p <- alpha * op(B) op(X^p) op(A)^T + beta * Y^p         (Sec. 2.2)
+ *         op(A): ma x na, op(B): mb x nb, op(X^p): nb x na, Y^p: mb x ma.
+ *   3-D:  Y^p[i,j,k] <- alpha * sum_{l,m,q} op(C)[i,l] op(B)[j,m] op(A)[k,q]
+ *                       X^p[l,m,q] + beta * Y^p[i,j,k]                (Sec. 2.1-2.2)
+ *         X^p: nc x nb x na, Y^p: mc x mb x ma; C acts on mode 1, B on mode 2,
+ *         A on mode 3, i.e. vec(Y) = (op(A) (x) op(B) (x) op(C)) vec(X).
+ *
+ * Every array is column-major.  Leading dimensions follow the TKRON2/TKRON3
+ * interfaces of Sec. 3: ldx (column stride), ldx2 (plane stride, 3-D) and ldxp
+ * (offset between consecutive batch instances), all in elements.
+ *
+ * beta == 0 means Y is not read (BLAS convention), so NaN in Y is ignored.
+ *
+ * Three independent evaluations are provided:
+ *   O1 "direct":   the multiple sum written out (Sec. 2.1 sums), O(n^4) / O(n^6)
+ *   O2 "factored": one mode at a time in the order of Algorithm 1 (first the
+ *                  2-D product on every plane, then the third mode)
+ *   O3 "matrix":   the explicit Kronecker matrix from the block definition of
+ *                  Sec. 2, for tiny sizes, to be multiplied with vec(X).
+ *
+ * FP64 and FP32 variants; the FP32 variants accumulate in float and the file
+ * is compiled with -ffp-contract=off so no fused multiply-add is formed.
+ */
+#include <stddef.h>
+#include <stdint.h>
+
+#define ORACLE_API __attribute__((visibility("default")))
+
+/* op(M)[r, c] for a column-major stored matrix with leading dimension ld. */
+#define OPEL(M, ld, t, r, c) (((t) == 'N' || (t) == 'n') ? (M)[(size_t)(r) + (size_t)(ld) * (size_t)(c)] \
+                                                        : (M)[(size_t)(c) + (size_t)(ld) * (size_t)(r)])
+
+#define DEFINE_ORACLE(T, SUF)                                                                  \
+/* O1, 2-D: Y[i,j] = alpha * sum_l sum_m opB[i,l] opX[l,m] opA[j,m] + beta Y[i,j] (Sec. 2.1) */ \
+ORACLE_API void oracle_kron2_direct_##SUF(char ta, char tb, char tx, int ma, int na, int mb,   \
+    int nb, int64_t batch, T alpha, const T* A, int lda, const T* B, int ldb, const T* X,      \
+    int ldx, int64_t ldxp, T beta, T* Y, int ldy, int64_t ldyp)                                 \
+{                                                                                              \
+    int64_t p;                                                                                 \
+    _Pragma("omp parallel for schedule(static)")                                               \
+    for (p = 0; p < batch; p++) {                                                              \
+        const T* Xp = X + p * ldxp;                                                            \
+        T* Yp = Y + p * ldyp;                                                                  \
+        for (int j = 0; j < ma; j++)                                                           \
+            for (int i = 0; i < mb; i++) {                                                     \
+                T s = 0;                                                                       \
+                for (int l = 0; l < nb; l++)                                                   \
+                    for (int m = 0; m < na; m++)                                               \
+                        s += OPEL(B, ldb, tb, i, l) * OPEL(Xp, ldx, tx, l, m)                  \
+                             * OPEL(A, lda, ta, j, m);                                         \
+                T* y = &Yp[(size_t)i + (size_t)ldy * j];                                       \
+                *y = (beta == (T)0) ? alpha * s : alpha * s + beta * *y;                       \
+            }                                                                                  \
+    }                                                                                          \
+}                                                                                              \
+                                                                                               \
+/* O2, 2-D: Z = opB * opX (mb x na), then Y = alpha * Z * opA^T + beta * Y.                   \
+   The per-plane step of Algorithm 1, one small GEMM after the other. */                       \
+ORACLE_API void oracle_kron2_factored_##SUF(char ta, char tb, char tx, int ma, int na, int mb, \
+    int nb, int64_t batch, T alpha, const T* A, int lda, const T* B, int ldb, const T* X,      \
+    int ldx, int64_t ldxp, T beta, T* Y, int ldy, int64_t ldyp)                                 \
+{                                                                                              \
+    int64_t p;                                                                                 \
+    _Pragma("omp parallel for schedule(static)")                                               \
+    for (p = 0; p < batch; p++) {                                                              \
+        T Z[16 * 16];                                                                          \
+        const T* Xp = X + p * ldxp;                                                            \
+        T* Yp = Y + p * ldyp;                                                                  \
+        for (int m = 0; m < na; m++)                                                           \
+            for (int i = 0; i < mb; i++) {                                                     \
+                T s = 0;                                                                       \
+                for (int l = 0; l < nb; l++)                                                   \
+                    s += OPEL(B, ldb, tb, i, l) * OPEL(Xp, ldx, tx, l, m);                     \
+                Z[i + 16 * m] = s;                                                             \
+            }                                                                                  \
+        for (int j = 0; j < ma; j++)                                                           \
+            for (int i = 0; i < mb; i++) {                                                     \
+                T s = 0;                                                                       \
+                for (int m = 0; m < na; m++)                                                   \
+                    s += Z[i + 16 * m] * OPEL(A, lda, ta, j, m);                               \
+                T* y = &Yp[(size_t)i + (size_t)ldy * j];                                       \
+                *y = (beta == (T)0) ? alpha * s : alpha * s + beta * *y;                       \
+            }                                                                                  \
+    }                                                                                          \
+}                                                                                              \
+                                                                                               \
+/* O1, 3-D: the triple sum of Sec. 2.1, written out. */                                        \
+ORACLE_API void oracle_kron3_direct_##SUF(char ta, char tb, char tc, int ma, int na, int mb,   \
+    int nb, int mc, int nc, int64_t batch, T alpha, const T* A, int lda, const T* B, int ldb,  \
+    const T* C, int ldc, const T* X, int ldx, int ldx2, int64_t ldxp, T beta, T* Y, int ldy,   \
+    int ldy2, int64_t ldyp)                                                                    \
+{                                                                                              \
+    int64_t p;                                                                                 \
+    _Pragma("omp parallel for schedule(static)")                                               \
+    for (p = 0; p < batch; p++) {                                                              \
+        const T* Xp = X + p * ldxp;                                                            \
+        T* Yp = Y + p * ldyp;                                                                  \
+        for (int k = 0; k < ma; k++)                                                           \
+            for (int j = 0; j < mb; j++)                                                       \
+                for (int i = 0; i < mc; i++) {                                                 \
+                    T s = 0;                                                                   \
+                    for (int l = 0; l < nc; l++)                                               \
+                        for (int m = 0; m < nb; m++)                                           \
+                            for (int q = 0; q < na; q++)                                       \
+                                s += OPEL(C, ldc, tc, i, l) * OPEL(B, ldb, tb, j, m)           \
+                                     * OPEL(A, lda, ta, k, q)                                  \
+                                     * Xp[(size_t)l + (size_t)ldx * m + (size_t)ldx2 * q];     \
+                    T* y = &Yp[(size_t)i + (size_t)ldy * j + (size_t)ldy2 * k];                \
+                    *y = (beta == (T)0) ? alpha * s : alpha * s + beta * *y;                   \
+                }                                                                              \
+    }                                                                                          \
+}                                                                                              \
+                                                                                               \
+/* O2, 3-D, Algorithm 1: every plane q gets tmp(:,:,q) = opC * X(:,:,q) * opB^T               \
+   (the 2-D step), then each slice tmp(:,j,:) is multiplied by opA^T (the batched            \
+   GEMM step).  tmp is mc x mb x na. */                                                        \
+ORACLE_API void oracle_kron3_factored_##SUF(char ta, char tb, char tc, int ma, int na, int mb, \
+    int nb, int mc, int nc, int64_t batch, T alpha, const T* A, int lda, const T* B, int ldb,  \
+    const T* C, int ldc, const T* X, int ldx, int ldx2, int64_t ldxp, T beta, T* Y, int ldy,   \
+    int ldy2, int64_t ldyp)                                                                    \
+{                                                                                              \
+    int64_t p;                                                                                 \
+    _Pragma("omp parallel for schedule(static)")                                               \
+    for (p = 0; p < batch; p++) {                                                              \
+        T Z[16 * 16];                                                                          \
+        T tmp[16 * 16 * 16];                                                                   \
+        const T* Xp = X + p * ldxp;                                                            \
+        T* Yp = Y + p * ldyp;                                                                  \
+        for (int q = 0; q < na; q++) {                                                         \
+            const T* Xq = Xp + (size_t)ldx2 * q;                                               \
+            for (int m = 0; m < nb; m++)                                                       \
+                for (int i = 0; i < mc; i++) {                                                 \
+                    T s = 0;                                                                   \
+                    for (int l = 0; l < nc; l++)                                               \
+                        s += OPEL(C, ldc, tc, i, l) * Xq[(size_t)l + (size_t)ldx * m];         \
+                    Z[i + 16 * m] = s;                                                         \
+                }                                                                              \
+            for (int j = 0; j < mb; j++)                                                       \
+                for (int i = 0; i < mc; i++) {                                                 \
+                    T s = 0;                                                                   \
+                    for (int m = 0; m < nb; m++)                                               \
+                        s += Z[i + 16 * m] * OPEL(B, ldb, tb, j, m);                           \
+                    tmp[i + 16 * j + 256 * q] = s;                                             \
+                }                                                                              \
+        }                                                                                      \
+        for (int j = 0; j < mb; j++)                                                           \
+            for (int k = 0; k < ma; k++)                                                       \
+                for (int i = 0; i < mc; i++) {                                                 \
+                    T s = 0;                                                                   \
+                    for (int q = 0; q < na; q++)                                               \
+                        s += tmp[i + 16 * j + 256 * q] * OPEL(A, lda, ta, k, q);               \
+                    T* y = &Yp[(size_t)i + (size_t)ldy * j + (size_t)ldy2 * k];                \
+                    *y = (beta == (T)0) ? alpha * s : alpha * s + beta * *y;                   \
+                }                                                                              \
+    }                                                                                          \
+}
+
+DEFINE_ORACLE(double, f64)
+DEFINE_ORACLE(float, f32)
+
+/* O3: the Kronecker matrix K = A (x) B from the block definition of Sec. 2:
+ * block (r, c) of K is a_{rc} * B, so K[r*mb + i, c*nb + j] = A[r,c] * B[i,j].
+ * A is ma x na (lda), B is mb x nb (ldb); K is (ma*mb) x (na*nb), column-major,
+ * leading dimension ma*mb.  No op() here: callers transpose beforehand. */
+ORACLE_API void oracle_kron_matrix_f64(int ma, int na, int mb, int nb, const double* A, int lda,
+                                       const double* B, int ldb, double* K)
+{
+    const size_t ldk = (size_t)ma * (size_t)mb;
+    for (int r = 0; r < ma; r++)
+        for (int c = 0; c < na; c++)
+            for (int i = 0; i < mb; i++)
+                for (int j = 0; j < nb; j++)
+                    K[((size_t)r * mb + i) + ldk * ((size_t)c * nb + j)] =
+                        A[(size_t)r + (size_t)lda * c] * B[(size_t)i + (size_t)ldb * j];
+}
+
+/* Plain matrix-vector product y = K x for a column-major (rows x cols) K. */
+ORACLE_API void oracle_matvec_f64(int64_t rows, int64_t cols, const double* K, const double* x,
+                                  double* y)
+{
+    for (int64_t r = 0; r < rows; r++) {
+        double s = 0;
+        for (int64_t c = 0; c < cols; c++) s += K[r + rows * c] * x[c];
+        y[r] = s;
+    }
+}
+
+/* Threads the OpenMP runtime would use (1 when built without OpenMP). */
+ORACLE_API int oracle_num_threads(void)
+{
+#ifdef _OPENMP
+    extern int omp_get_max_threads(void);
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
