@@ -1,0 +1,200 @@
+/*
+ * kron.h -- C ABI of the GB300 batched Kronecker product library.
+ *
+ * Operation (paper Sec. 2.2, "Batched Kronecker products"): for p = 0..N-1
+ *
+ *   2-D:  vec(Y^p) <- alpha (op(A) (x) op(B)) vec(op(X^p)) + beta vec(Y^p)
+ *         i.e.  Y^p = alpha op(B) op(X^p) op(A)^T + beta Y^p          (Sec. 2, vec identity)
+ *   3-D:  vec(Y^p) <- alpha (op(A) (x) op(B) (x) op(C)) vec(X^p) + beta vec(Y^p)
+ *         i.e.  Y^p[i,j,k] = alpha sum_{l,m,q} op(C)[i,l] op(B)[j,m] op(A)[k,q] X^p[l,m,q]
+ *                            + beta Y^p[i,j,k]                          (Sec. 2.1, triple sum)
+ *
+ * The component matrices A, B (, C) are the same for the whole batch; the
+ * operands X^p and results Y^p vary (Sec. 2.2).  Arrays are column-major
+ * (Sec. 3).  The LAST Kronecker factor acts on the FASTEST (first) mode.
+ *
+ * Relation to the paper's TKRON2/TKRON3 (Sec. 3): the paper writes the 2-D
+ * operator as B (x) A with Y = A X B^T and the 3-D one as C (x) B (x) A with A on
+ * mode 1.  Hence   TKRON2(A, B, ...)    == kron2_batched(.., B, .., A, ..)
+ * and              TKRON3(A, B, C, ...) == kron3_batched(.., C, .., B, .., A, ..)
+ * (component arguments in reverse order; all other arguments keep their meaning).
+ *
+ * Conventions shared by every entry point
+ *  - Status codes are returned, never thrown; all validation happens before any
+ *    launch, so nothing is written when a call returns an error.
+ *  - X, Y: DEVICE pointers owned by the caller.  X is read-only.  X and Y must
+ *    not overlap (KRON_ERR_ALIAS); the operation is out of place.
+ *  - A, B, C: HOST pointers to the components, read during the call and passed
+ *    by value to the kernel (they are at most 3 x 16 x 16 values and constant
+ *    over the batch; Sec. 2.2 notes that transposing them once up front costs
+ *    little, which is what the library does).  After the call returns the host
+ *    arrays may be reused.  Type: float for KRON_R32F / KRON_R16BF / KRON_R16F
+ *    storage, double for KRON_R64F.
+ *  - alpha, beta: HOST pointers to scalars of the same type as the components.
+ *    beta == 0 means Y is not read (NaN/Inf in Y are ignored, BLAS convention).
+ *  - Leading dimensions are in elements (Sec. 3): ldx = column stride, ldx2 =
+ *    plane stride (3-D), ldxp = offset between consecutive instances ("uniform
+ *    offset from the previous entity").  ldxp may be 0 (one X for every p).
+ *  - Sizes: every dimension in 1..16 (the paper's range, Sec. 1).
+ *  - batch_count == 0 is a no-op returning KRON_OK.
+ *  - The library never allocates device memory inside these calls (Sec. 4,
+ *    work-array discussion): the fixed-size paths need no workspace and the
+ *    mixed-size path takes a caller-owned workspace.
+ *  - Calls are asynchronous on `stream` (NULL = legacy default stream).  A
+ *    launch failure is reported as KRON_ERR_CUDA.  Device-side waits are
+ *    bounded; an expired wait is recorded in a device status word read back by
+ *    kron_device_status().
+ */
+#ifndef KRON_GB300_H
+#define KRON_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define KRON_API __attribute__((visibility("default")))
+
+typedef struct CUstream_st* kron_stream_t; /* same type as cudaStream_t / CUstream */
+
+typedef enum {
+    KRON_OK = 0,
+    KRON_ERR_INVALID_VALUE = 1,   /* a size, stride, flag or pointer argument is invalid */
+    KRON_ERR_NOT_SUPPORTED = 2,   /* valid but not implemented (e.g. compute mode / dtype pair) */
+    KRON_ERR_ALIAS = 3,           /* the X and Y address ranges overlap */
+    KRON_ERR_WORKSPACE = 4,       /* workspace missing, too small or misaligned */
+    KRON_ERR_CUDA = 5,            /* a CUDA runtime call failed (launch, graph, device query) */
+    KRON_ERR_DEVICE_TIMEOUT = 6   /* a bounded device-side wait expired */
+} kron_status;
+
+/* Storage type of X and Y. */
+typedef enum {
+    KRON_R32F = 0,   /* float;  components/alpha/beta float  */
+    KRON_R64F = 1,   /* double; components/alpha/beta double */
+    KRON_R16BF = 2,  /* bfloat16 operands, FP32 accumulation; components float */
+    KRON_R16F = 3    /* float16 operands, FP32 accumulation; components float */
+} kron_dtype;
+
+/* How the contractions are computed. */
+typedef enum {
+    /* CUDA cores: FP32 FMA for R32F/R16BF/R16F storage, FP64 FMA for R64F. */
+    KRON_COMPUTE_NATIVE = 0,
+    /* Tensor cores, split precision: each FP32 value v = hi + lo with hi, lo
+       bfloat16 (round to nearest even); products hi*hi + hi*lo + lo*hi are
+       accumulated in FP32.  Valid for R32F and R16BF storage. */
+    KRON_COMPUTE_32F_BF16X3 = 1
+} kron_compute;
+
+KRON_API const char* kron_status_string(kron_status s);
+
+/* Library version as 10000*major + 100*minor + patch. */
+KRON_API int kron_version(void);
+
+/*
+ * kron2_batched -- the paper's TKRON2 (Sec. 3) with the component order above.
+ *
+ *   op(A): ma x na, stored as A (lda >= rows of the stored matrix: ma if
+ *          transa = 'N', na if 'T')
+ *   op(B): mb x nb, stored as B (ldb likewise)
+ *   op(X^p): nb x na; X^p is stored at X + p*ldxp with column stride ldx
+ *          (ldx >= nb if transx = 'N', >= na if 'T')
+ *   Y^p:   mb x ma at Y + p*ldyp, column stride ldy >= mb,
+ *          ldyp >= ldy*(ma-1) + mb (instances of Y must not overlap)
+ *   trans*: 'N'/'n' = no transpose, 'T'/'t' = transpose ('C'/'c' = 'T' for real data)
+ *
+ * Errors: KRON_ERR_INVALID_VALUE (bad size, ld, trans, null pointer with
+ * batch_count > 0, negative batch or stride), KRON_ERR_NOT_SUPPORTED (compute
+ * mode not available for io), KRON_ERR_ALIAS (X and Y ranges overlap),
+ * KRON_ERR_CUDA (launch failed).
+ */
+KRON_API kron_status kron2_batched(kron_stream_t stream, char transa, char transb, char transx,
+                                   int ma, int na, int mb, int nb, int64_t batch_count,
+                                   const void* alpha, const void* A, int lda, const void* B,
+                                   int ldb, const void* X, int ldx, int64_t ldxp,
+                                   const void* beta, void* Y, int ldy, int64_t ldyp,
+                                   kron_dtype io, kron_compute comp);
+
+/*
+ * kron3_batched -- the paper's TKRON3 (Sec. 3) with the component order above;
+ * like the paper, no transpose of X.
+ *
+ *   op(A): ma x na (mode 3), op(B): mb x nb (mode 2), op(C): mc x nc (mode 1)
+ *   X^p: nc x nb x na at X + p*ldxp, element (l,m,q) at l + ldx*m + ldx2*q,
+ *        ldx >= nc, ldx2 >= ldx*nb
+ *   Y^p: mc x mb x ma at Y + p*ldyp, element (i,j,k) at i + ldy*j + ldy2*k,
+ *        ldy >= mc, ldy2 >= ldy*mb, ldyp >= ldy2*(ma-1) + ldy*(mb-1) + mc
+ *
+ * The three mode contractions (Algorithm 1's 2-D step per plane, then the third
+ * mode) are fused in one kernel; no intermediate array goes to device memory.
+ * Errors: as kron2_batched.
+ */
+KRON_API kron_status kron3_batched(kron_stream_t stream, char transa, char transb, char transc,
+                                   int ma, int na, int mb, int nb, int mc, int nc,
+                                   int64_t batch_count, const void* alpha, const void* A, int lda,
+                                   const void* B, int ldb, const void* C, int ldc, const void* X,
+                                   int ldx, int ldx2, int64_t ldxp, const void* beta, void* Y,
+                                   int ldy, int ldy2, int64_t ldyp, kron_dtype io,
+                                   kron_compute comp);
+
+/*
+ * kron_device_status -- synchronises `stream`, then reads and clears the
+ * device status word of the current device.  Returns KRON_OK, or
+ * KRON_ERR_DEVICE_TIMEOUT if a kernel gave up on a bounded wait since the last
+ * call (its outputs for that launch are then incomplete), or KRON_ERR_CUDA.
+ */
+KRON_API kron_status kron_device_status(kron_stream_t stream);
+
+/*
+ * Mixed-size batches (one launch for instances of different sizes and kinds).
+ *
+ * A class is one (kind, n) pair with its own shared components (square n x n,
+ * column-major, host pointers, 'N' op; C only for kind 3).  A plan may hold at
+ * most one class per (kind, n).  Instance p belongs to class h_class_of[p];
+ * its operand starts at element offset h_x_off[p] of X and its result at
+ * h_y_off[p] of Y; instances are contiguous (minimal leading dimensions),
+ * alpha = 1, beta = 0.  Storage: KRON_R32F or KRON_R16BF / KRON_R16F
+ * (components float).
+ *
+ * kron_varlen_plan_create copies the host metadata, sorts instances by class,
+ * chooses per-class tile sizes (from the tuning cache when present) and
+ * prepares the device tables; it launches nothing.  The tables live in the
+ * caller's workspace (kron_varlen_workspace_size bytes, 256-byte aligned
+ * device memory), written by the first execute on that workspace.
+ * kron_varlen_execute launches ONE persistent kernel, captured once into a CUDA
+ * graph and replayed with cudaGraphLaunch on later calls.
+ * kron_varlen_tune times the candidate tile sizes on the given buffers (it
+ * overwrites Y), keeps the fastest per class, records them in the tuning cache
+ * (file named by the KRON_TUNE_CACHE environment variable, if set) and
+ * re-captures the graph.
+ */
+typedef struct {
+    int kind;          /* 2 or 3 */
+    int n;             /* 1..16 */
+    const void* A;     /* host, n*n; mode 2 (kind 2) or mode 3 (kind 3) */
+    const void* B;     /* host, n*n; mode 1 (kind 2) or mode 2 (kind 3) */
+    const void* C;     /* host, n*n; mode 1 (kind 3), ignored for kind 2 */
+} kron_class_desc;
+
+typedef struct kron_varlen_plan kron_varlen_plan;
+
+KRON_API kron_status kron_varlen_plan_create(kron_varlen_plan** plan, int num_classes,
+                                             const kron_class_desc* classes, int64_t batch_count,
+                                             const int32_t* h_class_of, const int64_t* h_x_off,
+                                             const int64_t* h_y_off, kron_dtype io,
+                                             kron_compute comp);
+KRON_API kron_status kron_varlen_workspace_size(const kron_varlen_plan* plan, size_t* bytes);
+KRON_API kron_status kron_varlen_execute(kron_varlen_plan* plan, const void* X, void* Y,
+                                         void* workspace, size_t workspace_bytes,
+                                         kron_stream_t stream);
+KRON_API kron_status kron_varlen_tune(kron_varlen_plan* plan, const void* X, void* Y,
+                                      void* workspace, size_t workspace_bytes,
+                                      kron_stream_t stream);
+KRON_API kron_status kron_varlen_plan_destroy(kron_varlen_plan* plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KRON_GB300_H */

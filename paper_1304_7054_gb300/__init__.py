@@ -1,0 +1,176 @@
+"""Python binding of the GB300 batched Kronecker product library.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of ``_build/libkron_gb300.so`` (C ABI in ``include/kron.h``).  PyTorch
+provides device memory and streams.  There is no CPU fallback: if the library
+is missing or cannot be loaded, every call raises.
+
+Operation (paper Sec. 2.2):
+    kron2_batched:  Y^p <- alpha op(B) op(X^p) op(A)^T + beta Y^p
+                    ( = alpha (op(A) (x) op(B)) vec(op(X^p)) + beta vec(Y^p) )
+    kron3_batched:  Y^p <- alpha (op(A) (x) op(B) (x) op(C)) vec(X^p) + beta Y^p
+                    (C on mode 1, B on mode 2, A on mode 3)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libkron_gb300.so")
+
+KRON_OK = 0
+STATUS = {0: "KRON_OK", 1: "KRON_ERR_INVALID_VALUE", 2: "KRON_ERR_NOT_SUPPORTED", 3: "KRON_ERR_ALIAS",
+          4: "KRON_ERR_WORKSPACE", 5: "KRON_ERR_CUDA", 6: "KRON_ERR_DEVICE_TIMEOUT"}
+DTYPES = {"f32": 0, "f64": 1, "bf16": 2, "f16": 3}
+COMPUTE = {"native": 0, "bf16x3": 1}
+
+# Every entry point declared in include/kron.h, with its ctypes signature.
+_I, _L, _P, _C, _S = ctypes.c_int, ctypes.c_int64, ctypes.c_void_p, ctypes.c_char, ctypes.c_size_t
+SIGNATURES = {
+    "kron_status_string": ([_I], ctypes.c_char_p),
+    "kron_version": ([], _I),
+    "kron2_batched": ([_P, _C, _C, _C, _I, _I, _I, _I, _L, _P, _P, _I, _P, _I, _P, _I, _L, _P, _P, _I, _L,
+                       _I, _I], _I),
+    "kron3_batched": ([_P, _C, _C, _C, _I, _I, _I, _I, _I, _I, _L, _P, _P, _I, _P, _I, _P, _I, _P, _I, _I,
+                       _L, _P, _P, _I, _I, _L, _I, _I], _I),
+    "kron_device_status": ([_P], _I),
+    "kron_varlen_plan_create": ([ctypes.POINTER(_P), _I, _P, _L, _P, _P, _P, _I, _I], _I),
+    "kron_varlen_workspace_size": ([_P, ctypes.POINTER(_S)], _I),
+    "kron_varlen_execute": ([_P, _P, _P, _P, _S, _P], _I),
+    "kron_varlen_tune": ([_P, _P, _P, _P, _S, _P], _I),
+    "kron_varlen_plan_destroy": ([_P], _I),
+}
+
+_lib = None
+
+
+class KronError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {STATUS.get(status, status)}")
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load the CUDA library and bind the C ABI (raises if it is not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library not built: {path} is missing "
+                               "(run __graft_entry__.build() or paper_1304_7054_gb300/build.py)")
+        lib = ctypes.CDLL(path)
+        for name, (args, res) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+    return _lib
+
+
+def status_string(status: int) -> str:
+    return load_library().kron_status_string(status).decode()
+
+
+def _check(status: int, what: str):
+    if status != KRON_OK:
+        raise KronError(status, what)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _io_of(t) -> int:
+    torch = _torch()
+    m = {torch.float32: "f32", torch.float64: "f64", torch.bfloat16: "bf16", torch.float16: "f16"}
+    if t.dtype not in m:
+        raise TypeError(f"unsupported storage dtype {t.dtype}")
+    return DTYPES[m[t.dtype]]
+
+
+def _stream_handle(stream) -> int:
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _comp_buffer(M, ctype):
+    """A component as a host buffer: 2-D arrays become column-major (ld = rows);
+    1-D arrays are taken as already column-major.  Returns (array, ld)."""
+    if hasattr(M, "detach"):
+        M = M.detach().cpu().numpy()
+    M = np.asarray(M, dtype=ctype)
+    if M.ndim == 2:
+        return np.ascontiguousarray(M.T).ravel(), M.shape[0]
+    return np.ascontiguousarray(M.ravel()), None
+
+
+def _scalar(v, ctype):
+    return (ctypes.c_double if ctype == np.float64 else ctypes.c_float)(v)
+
+
+def kron2_batched(A, B, X, Y, *, ma, na, mb, nb, batch, alpha=1.0, beta=0.0, transa="N", transb="N",
+                  transx="N", lda=None, ldb=None, ldx=None, ldxp=None, ldy=None, ldyp=None,
+                  compute="native", stream=None):
+    """Y^p <- alpha op(B) op(X^p) op(A)^T + beta Y^p on CUDA tensors X, Y (storage
+    f32/f64/bf16/f16, flat column-major instances); A, B host arrays."""
+    L = load_library()
+    io = _io_of(X)
+    if _io_of(Y) != io:
+        raise TypeError("X and Y must have the same dtype")
+    ctype = np.float64 if io == DTYPES["f64"] else np.float32
+    Ab, lda0 = _comp_buffer(A, ctype)
+    Bb, ldb0 = _comp_buffer(B, ctype)
+    ta, tb, tx = transa.upper(), transb.upper(), transx.upper()
+    lda = lda or lda0 or (ma if ta == "N" else na)
+    ldb = ldb or ldb0 or (mb if tb == "N" else nb)
+    ldx = ldx or (nb if tx == "N" else na)
+    ldxp = ldx * (na if tx == "N" else nb) if ldxp is None else ldxp
+    ldy = ldy or mb
+    ldyp = ldy * ma if ldyp is None else ldyp
+    al, be = _scalar(alpha, ctype), _scalar(beta, ctype)
+    st = L.kron2_batched(_stream_handle(stream), ta.encode(), tb.encode(), tx.encode(), ma, na, mb, nb, batch,
+                         ctypes.addressof(al), Ab.ctypes.data, lda, Bb.ctypes.data, ldb, X.data_ptr(), ldx, ldxp,
+                         ctypes.addressof(be), Y.data_ptr(), ldy, ldyp, io, COMPUTE[compute])
+    _check(st, "kron2_batched")
+    return Y
+
+
+def kron3_batched(A, B, C, X, Y, *, ma, na, mb, nb, mc, nc, batch, alpha=1.0, beta=0.0, transa="N",
+                  transb="N", transc="N", lda=None, ldb=None, ldc=None, ldx=None, ldx2=None, ldxp=None,
+                  ldy=None, ldy2=None, ldyp=None, compute="native", stream=None):
+    """Y^p <- alpha (op(A) (x) op(B) (x) op(C)) vec(X^p) + beta Y^p (C on mode 1)."""
+    L = load_library()
+    io = _io_of(X)
+    if _io_of(Y) != io:
+        raise TypeError("X and Y must have the same dtype")
+    ctype = np.float64 if io == DTYPES["f64"] else np.float32
+    Ab, lda0 = _comp_buffer(A, ctype)
+    Bb, ldb0 = _comp_buffer(B, ctype)
+    Cb, ldc0 = _comp_buffer(C, ctype)
+    ta, tb, tc = transa.upper(), transb.upper(), transc.upper()
+    lda = lda or lda0 or (ma if ta == "N" else na)
+    ldb = ldb or ldb0 or (mb if tb == "N" else nb)
+    ldc = ldc or ldc0 or (mc if tc == "N" else nc)
+    ldx = ldx or nc
+    ldx2 = ldx2 or ldx * nb
+    ldxp = ldx2 * na if ldxp is None else ldxp
+    ldy = ldy or mc
+    ldy2 = ldy2 or ldy * mb
+    ldyp = ldy2 * ma if ldyp is None else ldyp
+    al, be = _scalar(alpha, ctype), _scalar(beta, ctype)
+    st = L.kron3_batched(_stream_handle(stream), ta.encode(), tb.encode(), tc.encode(), ma, na, mb, nb, mc, nc,
+                         batch, ctypes.addressof(al), Ab.ctypes.data, lda, Bb.ctypes.data, ldb, Cb.ctypes.data,
+                         ldc, X.data_ptr(), ldx, ldx2, ldxp, ctypes.addressof(be), Y.data_ptr(), ldy, ldy2, ldyp,
+                         io, COMPUTE[compute])
+    _check(st, "kron3_batched")
+    return Y
+
+
+def device_status(stream=None) -> int:
+    """Synchronise and read/clear the device status word (0 = OK)."""
+    return load_library().kron_device_status(_stream_handle(stream))

@@ -1,0 +1,263 @@
+// C ABI entry points: argument validation, component preparation (op() applied
+// once on the host, paper Sec. 2.2), choice of kernel, and the device status word.
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "kron_device.cuh"
+#include "kron_internal.h"
+
+namespace kron {
+
+// Device status word (bit kDevErrTimeout = a bounded device-side wait expired).
+__device__ unsigned g_kron_device_error;
+
+size_t elem_size(kron_dtype t) {
+    switch (t) {
+        case KRON_R32F: return 4;
+        case KRON_R64F: return 8;
+        case KRON_R16BF:
+        case KRON_R16F: return 2;
+    }
+    return 0;
+}
+
+constexpr int kMaxDevices = 64;
+
+const DeviceInfo& device_info() {
+    static DeviceInfo info[kMaxDevices];
+    static std::mutex mu;
+    static DeviceInfo none;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return none;
+    std::lock_guard<std::mutex> lock(mu);
+    DeviceInfo& d = info[dev];
+    if (d.device != dev) {
+        int sms = 0, optin = 0, per_sm = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess)
+            return none;
+        d.sms = sms;
+        d.smem_per_block_optin = (size_t)optin;
+        d.smem_per_sm = (size_t)per_sm;
+        d.device = dev;
+    }
+    return d;
+}
+
+unsigned* device_error_word() {
+    static unsigned* ptr[kMaxDevices] = {};
+    static std::mutex mu;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_kron_device_error) != cudaSuccess) return nullptr;
+        ptr[dev] = static_cast<unsigned*>(p);
+    }
+    return ptr[dev];
+}
+
+static bool trans_flag(char t, int* is_t) {
+    switch (t) {
+        case 'N': case 'n': *is_t = 0; return true;
+        case 'T': case 't': case 'C': case 'c': *is_t = 1; return true;
+        default: return false;
+    }
+}
+
+static bool dim_ok(int v) { return v >= 1 && v <= kMaxN; }
+
+// op(M) (rows x cols) from the stored matrix (leading dimension ld), zero-padded
+// into an N x N column-major block.
+static void op_pad(double* out, int N, const void* M, int ld, int is_t, int rows, int cols, bool dbl) {
+    for (int e = 0; e < N * N; ++e) out[e] = 0.0;
+    for (int c = 0; c < cols; ++c)
+        for (int r = 0; r < rows; ++r) {
+            const size_t idx = is_t ? (size_t)c + (size_t)ld * r : (size_t)r + (size_t)ld * c;
+            out[r + N * c] = dbl ? static_cast<const double*>(M)[idx] : (double)static_cast<const float*>(M)[idx];
+        }
+}
+
+static bool ranges_overlap(const void* a, size_t abytes, const void* b, size_t bbytes) {
+    const uintptr_t a0 = (uintptr_t)a, b0 = (uintptr_t)b;
+    return a0 < b0 + bbytes && b0 < a0 + abytes;
+}
+
+static void choose_yvec(KronDesc& d) {
+    const size_t s = elem_size(d.io);
+    d.yvec = 0;
+    if (d.ye[0] != d.N) return;
+    for (int vb = 16; vb >= 4; vb /= 2) {
+        if ((size_t)vb < s) break;
+        const bool ok = (d.N * s) % vb == 0 && ((uintptr_t)d.Y) % vb == 0 && ((size_t)d.ldy * s) % vb == 0 &&
+                        (d.D == 2 || ((size_t)d.ldy2 * s) % vb == 0) && ((size_t)d.ldyp * s) % vb == 0;
+        if (ok) { d.yvec = vb; return; }
+    }
+}
+
+static kron_status dispatch(KronDesc& d, cudaStream_t st) {
+    if (d.comp == KRON_COMPUTE_32F_BF16X3) return launch_tc(d, st);
+    switch (d.io) {
+        case KRON_R32F: return d.D == 2 ? launch_fiber_f32_d2(d, st) : launch_fiber_f32_d3(d, st);
+        case KRON_R64F: return d.D == 2 ? launch_fiber_f64_d2(d, st) : launch_fiber_f64_d3(d, st);
+        case KRON_R16BF: return d.D == 2 ? launch_fiber_bf16_d2(d, st) : launch_fiber_bf16_d3(d, st);
+        case KRON_R16F: return d.D == 2 ? launch_fiber_f16_d2(d, st) : launch_fiber_f16_d3(d, st);
+    }
+    return KRON_ERR_INVALID_VALUE;
+}
+
+static kron_status check_modes(kron_dtype io, kron_compute comp) {
+    if (io != KRON_R32F && io != KRON_R64F && io != KRON_R16BF && io != KRON_R16F) return KRON_ERR_INVALID_VALUE;
+    if (comp == KRON_COMPUTE_NATIVE) return KRON_OK;
+    if (comp == KRON_COMPUTE_32F_BF16X3) return (io == KRON_R32F || io == KRON_R16BF) ? KRON_OK : KRON_ERR_NOT_SUPPORTED;
+    return KRON_ERR_INVALID_VALUE;
+}
+
+}  // namespace kron
+
+using namespace kron;
+
+extern "C" {
+
+KRON_API const char* kron_status_string(kron_status s) {
+    switch (s) {
+        case KRON_OK: return "KRON_OK";
+        case KRON_ERR_INVALID_VALUE: return "KRON_ERR_INVALID_VALUE";
+        case KRON_ERR_NOT_SUPPORTED: return "KRON_ERR_NOT_SUPPORTED";
+        case KRON_ERR_ALIAS: return "KRON_ERR_ALIAS";
+        case KRON_ERR_WORKSPACE: return "KRON_ERR_WORKSPACE";
+        case KRON_ERR_CUDA: return "KRON_ERR_CUDA";
+        case KRON_ERR_DEVICE_TIMEOUT: return "KRON_ERR_DEVICE_TIMEOUT";
+    }
+    return "KRON_ERR_UNKNOWN";
+}
+
+KRON_API int kron_version(void) { return 10000; }
+
+KRON_API kron_status kron2_batched(kron_stream_t stream, char transa, char transb, char transx, int ma, int na,
+                                   int mb, int nb, int64_t batch_count, const void* alpha, const void* A, int lda,
+                                   const void* B, int ldb, const void* X, int ldx, int64_t ldxp, const void* beta,
+                                   void* Y, int ldy, int64_t ldyp, kron_dtype io, kron_compute comp) {
+    int ta, tb, tx;
+    if (!trans_flag(transa, &ta) || !trans_flag(transb, &tb) || !trans_flag(transx, &tx))
+        return KRON_ERR_INVALID_VALUE;
+    if (!dim_ok(ma) || !dim_ok(na) || !dim_ok(mb) || !dim_ok(nb)) return KRON_ERR_INVALID_VALUE;
+    if (batch_count < 0 || ldxp < 0) return KRON_ERR_INVALID_VALUE;
+    kron_status st = check_modes(io, comp);
+    if (st != KRON_OK) return st;
+    if (lda < (ta ? na : ma) || ldb < (tb ? nb : mb)) return KRON_ERR_INVALID_VALUE;
+    const int xrows = tx ? na : nb, xcols = tx ? nb : na;
+    if (ldx < xrows || ldy < mb) return KRON_ERR_INVALID_VALUE;
+    if (ldyp < (int64_t)ldy * (ma - 1) + mb) return KRON_ERR_INVALID_VALUE;
+    if (!alpha || !beta) return KRON_ERR_INVALID_VALUE;
+    if (batch_count == 0) return KRON_OK;
+    if (!A || !B || !X || !Y) return KRON_ERR_INVALID_VALUE;
+    const size_t es = elem_size(io);
+    if (((uintptr_t)X) % es || ((uintptr_t)Y) % es) return KRON_ERR_INVALID_VALUE;
+    const size_t xbytes = ((size_t)(batch_count - 1) * ldxp + (size_t)ldx * (xcols - 1) + xrows) * es;
+    const size_t ybytes = ((size_t)(batch_count - 1) * ldyp + (size_t)ldy * (ma - 1) + mb) * es;
+    if (ranges_overlap(X, xbytes, Y, ybytes)) return KRON_ERR_ALIAS;
+
+    static thread_local KronDesc d;
+    d = KronDesc();
+    const bool dbl = io == KRON_R64F;
+    d.D = 2;
+    d.N = std::max(std::max(ma, na), std::max(mb, nb));
+    op_pad(d.m1, d.N, B, ldb, tb, mb, nb, dbl);
+    op_pad(d.m2, d.N, A, lda, ta, ma, na, dbl);
+    memset(d.m3, 0, sizeof(d.m3));
+    d.X = X;
+    d.Y = Y;
+    d.batch = batch_count;
+    d.ldx = ldx;
+    d.ldxp = ldxp;
+    d.ldy = ldy;
+    d.ldyp = ldyp;
+    d.ldx2 = 0;
+    d.ldy2 = 0;
+    d.transx = tx;
+    d.xe[0] = nb; d.xe[1] = na; d.xe[2] = 1;
+    d.ye[0] = mb; d.ye[1] = ma; d.ye[2] = 1;
+    d.alpha = dbl ? *static_cast<const double*>(alpha) : (double)*static_cast<const float*>(alpha);
+    d.beta = dbl ? *static_cast<const double*>(beta) : (double)*static_cast<const float*>(beta);
+    d.io = io;
+    d.comp = comp;
+    const int N = d.N;
+    d.contiguous = ma == N && na == N && mb == N && nb == N && !tx && ldx == N && ldxp == (int64_t)N * N &&
+                   ((uintptr_t)X) % 16 == 0;
+    choose_yvec(d);
+    return dispatch(d, (cudaStream_t)stream);
+}
+
+KRON_API kron_status kron3_batched(kron_stream_t stream, char transa, char transb, char transc, int ma, int na,
+                                   int mb, int nb, int mc, int nc, int64_t batch_count, const void* alpha,
+                                   const void* A, int lda, const void* B, int ldb, const void* C, int ldc,
+                                   const void* X, int ldx, int ldx2, int64_t ldxp, const void* beta, void* Y,
+                                   int ldy, int ldy2, int64_t ldyp, kron_dtype io, kron_compute comp) {
+    int ta, tb, tc;
+    if (!trans_flag(transa, &ta) || !trans_flag(transb, &tb) || !trans_flag(transc, &tc))
+        return KRON_ERR_INVALID_VALUE;
+    if (!dim_ok(ma) || !dim_ok(na) || !dim_ok(mb) || !dim_ok(nb) || !dim_ok(mc) || !dim_ok(nc))
+        return KRON_ERR_INVALID_VALUE;
+    if (batch_count < 0 || ldxp < 0) return KRON_ERR_INVALID_VALUE;
+    kron_status st = check_modes(io, comp);
+    if (st != KRON_OK) return st;
+    if (lda < (ta ? na : ma) || ldb < (tb ? nb : mb) || ldc < (tc ? nc : mc)) return KRON_ERR_INVALID_VALUE;
+    if (ldx < nc || (int64_t)ldx2 < (int64_t)ldx * nb) return KRON_ERR_INVALID_VALUE;
+    if (ldy < mc || (int64_t)ldy2 < (int64_t)ldy * mb) return KRON_ERR_INVALID_VALUE;
+    if (ldyp < (int64_t)ldy2 * (ma - 1) + (int64_t)ldy * (mb - 1) + mc) return KRON_ERR_INVALID_VALUE;
+    if (!alpha || !beta) return KRON_ERR_INVALID_VALUE;
+    if (batch_count == 0) return KRON_OK;
+    if (!A || !B || !C || !X || !Y) return KRON_ERR_INVALID_VALUE;
+    const size_t es = elem_size(io);
+    if (((uintptr_t)X) % es || ((uintptr_t)Y) % es) return KRON_ERR_INVALID_VALUE;
+    const size_t xbytes =
+        ((size_t)(batch_count - 1) * ldxp + (size_t)ldx2 * (na - 1) + (size_t)ldx * (nb - 1) + nc) * es;
+    const size_t ybytes =
+        ((size_t)(batch_count - 1) * ldyp + (size_t)ldy2 * (ma - 1) + (size_t)ldy * (mb - 1) + mc) * es;
+    if (ranges_overlap(X, xbytes, Y, ybytes)) return KRON_ERR_ALIAS;
+
+    static thread_local KronDesc d;
+    d = KronDesc();
+    const bool dbl = io == KRON_R64F;
+    d.D = 3;
+    d.N = std::max(std::max(std::max(ma, na), std::max(mb, nb)), std::max(mc, nc));
+    op_pad(d.m1, d.N, C, ldc, tc, mc, nc, dbl);
+    op_pad(d.m2, d.N, B, ldb, tb, mb, nb, dbl);
+    op_pad(d.m3, d.N, A, lda, ta, ma, na, dbl);
+    d.X = X;
+    d.Y = Y;
+    d.batch = batch_count;
+    d.ldx = ldx;
+    d.ldx2 = ldx2;
+    d.ldxp = ldxp;
+    d.ldy = ldy;
+    d.ldy2 = ldy2;
+    d.ldyp = ldyp;
+    d.transx = 0;
+    d.xe[0] = nc; d.xe[1] = nb; d.xe[2] = na;
+    d.ye[0] = mc; d.ye[1] = mb; d.ye[2] = ma;
+    d.alpha = dbl ? *static_cast<const double*>(alpha) : (double)*static_cast<const float*>(alpha);
+    d.beta = dbl ? *static_cast<const double*>(beta) : (double)*static_cast<const float*>(beta);
+    d.io = io;
+    d.comp = comp;
+    const int N = d.N;
+    d.contiguous = ma == N && na == N && mb == N && nb == N && mc == N && nc == N && ldx == N &&
+                   ldx2 == N * N && ldxp == (int64_t)N * N * N && ((uintptr_t)X) % 16 == 0;
+    choose_yvec(d);
+    return dispatch(d, (cudaStream_t)stream);
+}
+
+KRON_API kron_status kron_device_status(kron_stream_t stream) {
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return KRON_ERR_CUDA;
+    unsigned v = 0, zero = 0;
+    if (cudaMemcpyFromSymbol(&v, g_kron_device_error, sizeof(v)) != cudaSuccess) return KRON_ERR_CUDA;
+    if (v && cudaMemcpyToSymbol(g_kron_device_error, &zero, sizeof(zero)) != cudaSuccess) return KRON_ERR_CUDA;
+    return (v & kDevErrTimeout) ? KRON_ERR_DEVICE_TIMEOUT : KRON_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,8 @@
+// Instantiates the CUDA-core kernels for float storage, 2-D operands.
+#include "kron_fiber.cuh"
+
+namespace kron {
+kron_status launch_fiber_f32_d2(const KronDesc& d, cudaStream_t s) {
+    return launch_fiber_d<float, float, 2>(d, s);
+}
+}  // namespace kron

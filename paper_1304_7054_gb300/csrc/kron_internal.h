@@ -1,0 +1,71 @@
+// Host-side declarations shared by the translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/kron.h"
+
+namespace kron {
+
+constexpr int kMaxN = 16;
+constexpr int kFiberThreads = 256;   // threads per CTA of the CUDA-core kernels
+
+// One call, after validation: components already have op() applied and are
+// zero-padded to N x N (column-major); N = the largest dimension of the call.
+// Mode naming: M1 acts on mode 1 (the fastest index of X), M2 on mode 2, M3 on
+// mode 3.  2-D: M1 = op(B), M2 = op(A).  3-D: M1 = op(C), M2 = op(B), M3 = op(A).
+struct KronDesc {
+    int D = 2;          // 2 or 3
+    int N = 1;          // padded size, 1..16
+    double m1[kMaxN * kMaxN];
+    double m2[kMaxN * kMaxN];
+    double m3[kMaxN * kMaxN];
+    const void* X = nullptr;
+    void* Y = nullptr;
+    int64_t batch = 0, ldxp = 0, ldyp = 0;
+    int ldx = 0, ldx2 = 0, ldy = 0, ldy2 = 0;
+    int xe[3] = {1, 1, 1};   // extents of op(X) per mode
+    int ye[3] = {1, 1, 1};   // extents of Y per mode
+    int transx = 0;
+    double alpha = 1.0, beta = 0.0;
+    kron_dtype io = KRON_R32F;
+    kron_compute comp = KRON_COMPUTE_NATIVE;
+    // derived by the dispatcher
+    int contiguous = 0;  // square, minimal leading dims, 16-B aligned X: bulk-copy tiles
+    int yvec = 0;        // Y fiber store chunk in bytes (0 = element stores)
+    // launch configuration (0 = choose automatically)
+    int P = 0;           // instances per tile
+    int nstage = -1;     // bulk-copy pipeline depth; 0 = generic loads; -1 = auto
+    int grid = 0;        // CTAs; 0 = persistent (all resident CTAs)
+};
+
+size_t elem_size(kron_dtype t);
+
+// Device status word of the current device (device pointer).
+unsigned* device_error_word();
+
+// CUDA-core (fiber) kernels, one entry per storage type and kind (one
+// translation unit each, so they compile in parallel).
+kron_status launch_fiber_f32_d2(const KronDesc& d, cudaStream_t s);
+kron_status launch_fiber_f32_d3(const KronDesc& d, cudaStream_t s);
+kron_status launch_fiber_f64_d2(const KronDesc& d, cudaStream_t s);
+kron_status launch_fiber_f64_d3(const KronDesc& d, cudaStream_t s);
+kron_status launch_fiber_bf16_d2(const KronDesc& d, cudaStream_t s);
+kron_status launch_fiber_bf16_d3(const KronDesc& d, cudaStream_t s);
+kron_status launch_fiber_f16_d2(const KronDesc& d, cudaStream_t s);
+kron_status launch_fiber_f16_d3(const KronDesc& d, cudaStream_t s);
+
+// Tensor-core split-precision kernels (R32F or R16BF storage).
+kron_status launch_tc(const KronDesc& d, cudaStream_t s);
+
+// SM count and per-SM shared memory of the current device (cached).
+struct DeviceInfo {
+    int device = -1;
+    int sms = 0;
+    size_t smem_per_block_optin = 0;
+    size_t smem_per_sm = 0;
+};
+const DeviceInfo& device_info();
+
+}  // namespace kron

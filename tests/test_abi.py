@@ -1,0 +1,97 @@
+"""The C ABI on the host: the library loads, exports every declared entry point,
+and rejects invalid arguments with the documented status codes before touching
+the GPU (these calls run without a GPU)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1304_7054_gb300 as kg
+from paper_1304_7054_gb300 import build as libbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    libbuild.build()   # incremental: a no-op when up to date
+    return kg.load_library()
+
+
+def declared_symbols():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            names += re.findall(r"KRON_API\s+[\w\s\*]+?\b(\w+)\s*\(", src)
+    return names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_symbols()
+    assert "kron2_batched" in names and "kron3_batched" in names
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) <= set(kg.SIGNATURES), "binding misses a declared entry point"
+
+
+def test_status_strings(lib):
+    for code, name in kg.STATUS.items():
+        assert kg.status_string(code) == name
+
+
+F = ctypes.c_float(1.0)
+ZERO = ctypes.c_float(0.0)
+COMP = np.eye(16, dtype=np.float32).ravel()
+
+
+def k2(lib, **over):
+    a = dict(stream=None, ta=b"N", tb=b"N", tx=b"N", ma=4, na=4, mb=4, nb=4, batch=10,
+             alpha=ctypes.addressof(F), A=COMP.ctypes.data, lda=4, B=COMP.ctypes.data, ldb=4,
+             X=0x10000, ldx=4, ldxp=16, beta=ctypes.addressof(ZERO), Y=0x90000, ldy=4, ldyp=16,
+             io=0, comp=0)
+    a.update(over)
+    return lib.kron2_batched(*a.values())
+
+
+def k3(lib, **over):
+    a = dict(stream=None, ta=b"N", tb=b"N", tc=b"N", ma=3, na=3, mb=3, nb=3, mc=3, nc=3, batch=10,
+             alpha=ctypes.addressof(F), A=COMP.ctypes.data, lda=3, B=COMP.ctypes.data, ldb=3,
+             C=COMP.ctypes.data, ldc=3, X=0x10000, ldx=3, ldx2=9, ldxp=27, beta=ctypes.addressof(ZERO),
+             Y=0x90000, ldy=3, ldy2=9, ldyp=27, io=0, comp=0)
+    a.update(over)
+    return lib.kron3_batched(*a.values())
+
+
+INVALID, NOTSUP, ALIAS = 1, 2, 3
+
+
+@pytest.mark.parametrize("over,code", [
+    (dict(ma=0), INVALID), (dict(nb=17), INVALID), (dict(ta=b"X"), INVALID), (dict(tx=b"Q"), INVALID),
+    (dict(batch=-1), INVALID), (dict(lda=3), INVALID), (dict(ldb=2), INVALID), (dict(ldx=3), INVALID),
+    (dict(ldy=3), INVALID), (dict(ldyp=15), INVALID), (dict(ldxp=-1), INVALID),
+    (dict(alpha=None), INVALID), (dict(beta=None), INVALID), (dict(X=None), INVALID), (dict(Y=None), INVALID),
+    (dict(A=None), INVALID), (dict(io=7), INVALID), (dict(comp=9), INVALID),
+    (dict(io=1, comp=1), NOTSUP), (dict(io=3, comp=1), NOTSUP),
+    (dict(Y=0x10000 + 4 * 100), ALIAS), (dict(X=0x90000), ALIAS),
+    (dict(X=0x10002), INVALID),            # not aligned to the element size
+    (dict(ta=b"T", lda=3, ma=3, na=4), INVALID),   # stored A is na x ma: lda >= na
+    (dict(batch=0, X=None, Y=None), 0),    # empty batch: no-op
+])
+def test_kron2_validation(lib, over, code):
+    assert k2(lib, **over) == code
+
+
+@pytest.mark.parametrize("over,code", [
+    (dict(mc=0), INVALID), (dict(ldx2=8), INVALID), (dict(ldy2=8), INVALID), (dict(ldyp=26), INVALID),
+    (dict(C=None), INVALID), (dict(ldc=2), INVALID), (dict(Y=0x10000 + 8), ALIAS),
+    (dict(io=2, comp=0, X=0x10000, Y=0x90000), "launch"), (dict(batch=0), 0),
+])
+def test_kron3_validation(lib, over, code):
+    r = k3(lib, **over)
+    if code == "launch":
+        assert r != INVALID and r != NOTSUP   # valid arguments: only the launch itself can fail here
+    else:
+        assert r == code
