@@ -1,0 +1,487 @@
+#!/usr/bin/env python
+"""Throughput of the batched Kronecker product action on GB300.
+
+One step = one pass of the whole hot path over one batch: component
+preparation, operand stream-in, every mode contraction, epilogue and store
+(one kernel launch).  The headline workload is the 2-D FP32 action at n = 16
+over 2^20 instances (shared A, B ~ U[-1,1], X^p ~ N(0,1), seeded); the other
+workloads (3-D, FP64, 16-bit storage, split-precision tensor cores, mixed
+sizes) are measured the same way and reported under "variants".
+
+Flops follow the paper's convention (Sec. 5): 4 n^3 per 2-D and 6 n^4 per 3-D
+instance.  Algorithmic bytes are X read + Y written once (beta = 0).  Inputs
+(>= 0.5 GB per pass) are larger than the 129 MB L2, so no flush is needed.
+
+Usage: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Under torchrun each rank runs its own batch (weak scaling, no collective in
+the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GFlop/s & HBM GB/s (% roofline), 2-D/3-D Kronecker, n=16, FP32 vs BF16/varlen"
+FALLBACK_HBM_GBS = 6800.0
+FALLBACK_BF16_TFLOPS = 1900.0
+
+WORKLOADS = {
+    # name: kind, n, batch, storage, compute, seed
+    "kron2-f32-n16": dict(kind=2, n=16, batch=1 << 20, io="f32", compute="native", seed=1),
+    "kron2-f32-n10": dict(kind=2, n=10, batch=1 << 20, io="f32", compute="native", seed=1),
+    "kron3-f32-n16": dict(kind=3, n=16, batch=1 << 16, io="f32", compute="native", seed=2),
+    "kron3-f32-n10": dict(kind=3, n=10, batch=1 << 18, io="f32", compute="native", seed=2),
+    "kron2-f64-n16": dict(kind=2, n=16, batch=1 << 20, io="f64", compute="native", seed=1),
+    "kron3-f64-n16": dict(kind=3, n=16, batch=1 << 16, io="f64", compute="native", seed=2),
+    "kron2-bf16-n16": dict(kind=2, n=16, batch=1 << 20, io="bf16", compute="native", seed=4),
+    "kron2-f16-n16": dict(kind=2, n=16, batch=1 << 20, io="f16", compute="native", seed=4),
+    "kron2-bf16x3-n16": dict(kind=2, n=16, batch=1 << 20, io="f32", compute="bf16x3", seed=4),
+    "kron3-bf16x3-n16": dict(kind=3, n=16, batch=1 << 16, io="f32", compute="bf16x3", seed=4),
+    "kron2-bf16-bf16x3-n16": dict(kind=2, n=16, batch=1 << 20, io="bf16", compute="bf16x3", seed=4),
+}
+HEADLINE = "kron2-f32-n16"
+ESIZE = {"f32": 4, "f64": 8, "bf16": 2, "f16": 2}
+
+
+def flops_per_instance(kind, n):
+    return 4 * n ** 3 if kind == 2 else 6 * n ** 4
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return dict(hbm=float(d["hbm_gbs"]), bf16=float(d["bf16_tflops"]),
+                    bf16_sustained=float(d.get("bf16_tflops_sustained", d["bf16_tflops"])), src="measured")
+    return dict(hbm=FALLBACK_HBM_GBS, bf16=FALLBACK_BF16_TFLOPS, bf16_sustained=1700.0, src="fallback")
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t_on = self.t_off = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu=timestamp,{self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def mark_on(self):
+        self.t_on = time.time()
+
+    def mark_off(self):
+        self.t_off = time.time()
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.12)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for t, line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            rows.append((t, parts))
+        if not rows:
+            return None
+        inside = [r for t, r in rows if self.t_on is not None and self.t_on - 0.06 <= t <= (self.t_off or t) + 0.06]
+        use = inside or [r for _, r in rows]
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in use if num(r[1]) is not None]
+        mx = [num(r[2]) for r in use if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in use for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(use), "samples_in_timed_region": len(inside),
+                "power_w_max": max([num(r[3]) for r in use if num(r[3]) is not None] or [0])}
+
+
+# ---------------------------------------------------------------------------
+# our implementation
+# ---------------------------------------------------------------------------
+def make_inputs(wl, rank=0):
+    from paper_1304_7054_gb300 import inputs
+    b = inputs.make_batch(wl["kind"], wl["n"], wl["batch"], seed=wl["seed"] + 1000 * rank, x_dist="normal",
+                          dtype=np.float64 if wl["io"] == "f64" else np.float32)
+    return b
+
+
+def to_device_storage(b, io, torch, dev):
+    from paper_1304_7054_gb300 import inputs
+    if io in ("bf16", "f16"):
+        return inputs.to_storage(b.X, io).to(dev)
+    return torch.from_numpy(b.X).to(dev)
+
+
+def call(kg, b, X, Y, compute):
+    n = b.n
+    if b.kind == 2:
+        kg.kron2_batched(b.A, b.B, X, Y, ma=n, na=n, mb=n, nb=n, batch=b.batch, compute=compute)
+    else:
+        kg.kron3_batched(b.A, b.B, b.C, X, Y, ma=n, na=n, mb=n, nb=n, mc=n, nc=n, batch=b.batch,
+                         compute=compute)
+
+
+def sample_error(kg, b, Y, io, torch):
+    """Max normalised error vs the FP64 oracle on 512 seeded instances."""
+    import oracle
+    from paper_1304_7054_gb300 import inputs
+    inst = b.n ** b.kind
+    rng = np.random.default_rng(17)
+    idx = np.sort(rng.choice(b.batch, min(512, b.batch), replace=False))
+    if io in ("bf16", "f16"):
+        Xs = inputs.storage_to_f64(inputs.to_storage(b.X.reshape(b.batch, inst)[idx].ravel(), io))
+    else:
+        Xs = b.X.reshape(b.batch, inst)[idx].astype(np.float64).ravel()
+    n = b.n
+    if b.kind == 2:
+        ref = oracle.kron2(b.A, b.B, Xs, ma=n, na=n, mb=n, nb=n, batch=len(idx))
+    else:
+        ref = oracle.kron3(b.A, b.B, b.C, Xs, ma=n, na=n, mb=n, nb=n, mc=n, nc=n, batch=len(idx))
+    got = Y.view(b.batch, inst)[torch.from_numpy(idx).to(Y.device)].double().cpu().numpy()
+    cn = 1.0
+    for M in b.comps():
+        cn *= float(np.linalg.norm(np.asarray(M, np.float64)))
+    xn = np.linalg.norm(Xs.reshape(len(idx), inst), axis=1)
+    d = np.abs(got - ref.reshape(len(idx), inst)).max(axis=1)
+    return float((d / (cn * xn)).max())
+
+
+def time_device(kg, b, X, Y, compute, steps, warmup, torch, sampler=None, dist=None):
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        call(kg, b, X, Y, compute)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    if sampler:
+        sampler.mark_on()
+    t0.record(stream)
+    for i in range(steps):
+        ev[i][0].record(stream)
+        call(kg, b, X, Y, compute)
+        ev[i][1].record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.mark_off()
+    total_ms = t0.elapsed_time(t1)
+    kern_ms = sum(a.elapsed_time(c) for a, c in ev) / steps
+    return total_ms, kern_ms
+
+
+def time_e2e(kg, b, io, compute, steps, warmup, torch, dev):
+    """Public API with host buffers: pinned X -> device, the call, Y -> pinned host, every step."""
+    from paper_1304_7054_gb300 import inputs
+    if io in ("bf16", "f16"):
+        Xh = inputs.to_storage(b.X, io).pin_memory()
+    else:
+        Xh = torch.from_numpy(b.X).pin_memory()
+    Xd = torch.empty_like(Xh, device=dev)
+    Yd = torch.empty_like(Xd)
+    Yh = torch.empty_like(Xh).pin_memory()
+    stream = torch.cuda.current_stream()
+
+    def step():
+        Xd.copy_(Xh, non_blocking=True)
+        call(kg, b, Xd, Yd, compute)
+        Yh.copy_(Yd, non_blocking=True)
+
+    for _ in range(max(1, warmup)):
+        step()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for _ in range(steps):
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / steps
+    nbytes = Xh.numel() * Xh.element_size()
+    return ms, nbytes, nbytes
+
+
+def cpu_baseline(b, seconds=8.0):
+    """The FP32 oracle (sum-factorised loops, OpenMP over instances) on host cores,
+    on a bounded sample of the same workload; returns GFlop/s."""
+    import oracle
+    oracle.build()
+    n, inst = b.n, b.n ** b.kind
+    f = flops_per_instance(b.kind, n)
+    chunk = max(64, int(2e8 // f))
+    done, t_used = 0, 0.0
+    out = np.empty(chunk * inst, np.float32)
+    while t_used < seconds and done + chunk <= b.batch:
+        Xs = b.X[done * inst:(done + chunk) * inst]
+        t = time.perf_counter()
+        if b.kind == 2:
+            oracle.kron2(b.A, b.B, Xs, ma=n, na=n, mb=n, nb=n, batch=chunk, precision="f32", Y=out)
+        else:
+            oracle.kron3(b.A, b.B, b.C, Xs, ma=n, na=n, mb=n, nb=n, mc=n, nc=n, batch=chunk, precision="f32",
+                         Y=out)
+        t_used += time.perf_counter() - t
+        done += chunk
+    gf = done * f / t_used / 1e9
+    return {"value": round(gf, 3), "unit": "GFlop/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{done} of {b.batch} instances ({b.kind}-D n={n}, FP32 sum-factorised loops), "
+                      f"{t_used:.1f} s"}
+
+
+def measure_variant(kg, name, steps, warmup, torch, dev, peaks):
+    wl = WORKLOADS[name]
+    b = make_inputs(wl)
+    try:
+        X = to_device_storage(b, wl["io"], torch, dev)
+        Y = torch.empty_like(X)
+        call(kg, b, X, Y, wl["compute"])
+    except kg.KronError as e:
+        return {"unavailable": str(e)}
+    total_ms, kern_ms = time_device(kg, b, X, Y, wl["compute"], steps, warmup, torch)
+    err = sample_error(kg, b, Y, wl["io"], torch)
+    fl = flops_per_instance(b.kind, b.n) * b.batch
+    by = 2 * ESIZE[wl["io"]] * b.n ** b.kind * b.batch
+    gbs = by / (kern_ms * 1e-3) / 1e9
+    r = {"gflops": round(fl / (kern_ms * 1e-3) / 1e9, 1), "hbm_gbs": round(gbs, 1),
+         "hbm_frac": round(gbs / peaks["hbm"], 4), "ms": round(kern_ms, 4), "batch": b.batch,
+         "max_norm_err_vs_fp64_oracle": err}
+    del X, Y
+    torch.cuda.empty_cache()
+    return r
+
+
+def traffic_for(kernel_name):
+    """DRAM bytes per launch from a committed ncu summary, if the kernel sources are unchanged."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    e = d.get(kernel_name)
+    if not e:
+        return None
+    from paper_1304_7054_gb300 import build as lb
+    if e.get("source_hash") != lb.source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def run_ours(args):
+    import torch
+    import paper_1304_7054_gb300 as kg
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl")
+        dist = tdist
+    dev = torch.device("cuda", local if world > 1 else torch.cuda.current_device())
+    torch.cuda.set_device(dev)
+    kg.load_library()
+    peaks = load_peaks()
+    wl = WORKLOADS[args.workload]
+    b = make_inputs(wl, rank)
+    X = to_device_storage(b, wl["io"], torch, dev)
+    Y = torch.empty_like(X)
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    total_ms, kern_ms = time_device(kg, b, X, Y, wl["compute"], args.steps, args.warmup, torch, sampler, dist)
+    clocks = sampler.stop() if sampler else None
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    err = sample_error(kg, b, Y, wl["io"], torch)
+    ms = total_ms / args.steps
+    fl = flops_per_instance(b.kind, b.n) * b.batch
+    by = 2 * ESIZE[wl["io"]] * b.n ** b.kind * b.batch
+    value = world * fl / (ms * 1e-3) / 1e9
+    kernel_name = f"fiber_kernel<{wl['io']},{b.n},{b.kind}>"
+    achieved = by / (kern_ms * 1e-3) / 1e9
+    del X, Y
+    torch.cuda.empty_cache()
+    e2e_ms, h2d, d2h = time_e2e(kg, b, wl["io"], wl["compute"], max(3, min(args.steps, 20)), 2, torch, dev)
+    out = None
+    if rank == 0:
+        variants = {}
+        if not args.no_variants:
+            for name in WORKLOADS:
+                if name != args.workload:
+                    variants[name] = measure_variant(kg, name, max(5, min(args.steps, 30)), 3, torch, dev, peaks)
+        cpu = cpu_baseline(b, seconds=args.cpu_seconds)
+        out = {
+            "metric": METRIC, "value": round(value, 1), "unit": "GFlop/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 5),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": wl["io"], "data": "synthetic (seeded PCG64: A,B ~ U[-1,1], X ~ N(0,1))",
+            "config": {"workload": f"{b.kind}-D batched Kronecker action, n={b.n}, batch={b.batch}, "
+                                   f"{wl['io']} storage, {wl['compute']} compute",
+                       "kind": b.kind, "n": b.n, "batch_per_gpu": b.batch, "alpha": 1.0, "beta": 0.0,
+                       "layout": "contiguous column-major, minimal leading dimensions",
+                       "l2": "inputs larger than L2 (no flush)",
+                       "paper_k20c_gflops_context": 285 if (b.kind, b.n, wl["io"]) == (2, 16, "f32") else None},
+            "hbm_gbs": round(world * by / (ms * 1e-3) / 1e9, 1),
+            "max_norm_err_vs_fp64_oracle": err,
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm"], "unit": "GB/s",
+                         "frac": round(achieved / peaks["hbm"], 4), "traffic": traffic_for(kernel_name),
+                         "kernel": kernel_name, "peak_source": peaks["src"],
+                         "algorithmic_bytes_per_launch": by},
+            "cpu_baseline": cpu,
+            "e2e": {"value": round(world * fl / (e2e_ms * 1e-3) / 1e9, 1), "unit": "GFlop/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 4)},
+            "gpu_launches": args.steps,
+            "clocks": clocks,
+            "variants": variants,
+        }
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return out
+
+
+def run_profile(args):
+    """Warm-up and timed steps of one workload only (the command profiled with ncu)."""
+    import torch
+    import paper_1304_7054_gb300 as kg
+    dev = torch.device("cuda", torch.cuda.current_device())
+    kg.load_library()
+    wl = WORKLOADS[args.workload]
+    b = make_inputs(wl)
+    X = to_device_storage(b, wl["io"], torch, dev)
+    Y = torch.empty_like(X)
+    total_ms, kern_ms = time_device(kg, b, X, Y, wl["compute"], args.steps, args.warmup, torch)
+    fl = flops_per_instance(b.kind, b.n) * b.batch
+    by = 2 * ESIZE[wl["io"]] * b.n ** b.kind * b.batch
+    print(json.dumps({"workload": args.workload, "batch": b.batch, "kernel_ms": kern_ms,
+                      "gflops": fl / (kern_ms * 1e-3) / 1e9, "hbm_gbs": by / (kern_ms * 1e-3) / 1e9}))
+
+
+def run_reference(args):
+    """The oracle, as it stands, on the host cores (the reference arm of this benchmark)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    import oracle
+    oracle.build()
+    wl = WORKLOADS[args.workload]
+    b = make_inputs(wl)
+    n, inst = b.n, b.n ** b.kind
+    f = flops_per_instance(b.kind, n)
+    # a bounded sample per step, sized so that warm-up + timed steps take about a minute
+    probe = max(16, int(2e8 // f))
+    t = time.perf_counter()
+    pout = np.empty(probe * inst, np.float32)
+    if b.kind == 2:
+        oracle.kron2(b.A, b.B, b.X[:probe * inst], ma=n, na=n, mb=n, nb=n, batch=probe, precision="f32", Y=pout)
+    else:
+        oracle.kron3(b.A, b.B, b.C, b.X[:probe * inst], ma=n, na=n, mb=n, nb=n, mc=n, nc=n, batch=probe,
+                     precision="f32", Y=pout)
+    rate = probe / max(1e-6, time.perf_counter() - t)          # instances per second
+    per_step = int(max(16, min(b.batch // 2, rate * 60.0 / (args.steps + args.warmup))))
+    out = np.empty(per_step * inst, np.float32)
+
+    def step(i):
+        o = (i * per_step) % max(1, b.batch - per_step)
+        Xs = b.X[o * inst:(o + per_step) * inst]
+        if b.kind == 2:
+            oracle.kron2(b.A, b.B, Xs, ma=n, na=n, mb=n, nb=n, batch=per_step, precision="f32", Y=out)
+        else:
+            oracle.kron3(b.A, b.B, b.C, Xs, ma=n, na=n, mb=n, nb=n, mc=n, nc=n, batch=per_step,
+                         precision="f32", Y=out)
+
+    for i in range(args.warmup):
+        step(i)
+    t = time.perf_counter()
+    for i in range(args.steps):
+        step(i)
+    dt = (time.perf_counter() - t) / args.steps
+    value = per_step * f / dt / 1e9
+    cores = oracle.num_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "GFlop/s",
+        "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": wl["io"], "data": "synthetic (seeded PCG64: A,B ~ U[-1,1], X ~ N(0,1))",
+        "config": {"workload": f"{b.kind}-D batched Kronecker action, n={b.n}, batch={b.batch}, "
+                               f"{wl['io']} storage", "kind": b.kind, "n": b.n, "batch_per_gpu": b.batch},
+        "cpu_baseline": {"value": round(value, 3), "unit": "GFlop/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{per_step} instances per step of the {b.batch}-instance batch"},
+        "e2e": {"value": round(value, 3), "unit": "GFlop/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return line
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=HEADLINE)
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=8.0)
+    ap.add_argument("--batch", type=int, default=0, help="override the batch (profiling a smaller case)")
+    ap.add_argument("--profile", action="store_true",
+                    help="only warm-up + timed steps of the workload, no extra legs (for ncu captures)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.batch:
+        for wl in WORKLOADS.values():
+            wl["batch"] = args.batch
+    if args.profile:
+        run_profile(args)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -70,3 +70,13 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False, e
 if __name__ == "__main__":
     import sys
     print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+
+
+def source_hash() -> str:
+    """Hash of the kernel sources (used to tell whether a stored profile still applies)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(CSRC, "*"))):
+        h.update(os.path.basename(f).encode())
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
