@@ -101,6 +101,16 @@ static void choose_yvec(KronDesc& d) {
 
 static kron_status dispatch(KronDesc& d, cudaStream_t st) {
     if (d.comp == KRON_COMPUTE_32F_BF16X3) return launch_tc(d, st);
+    if (d.contiguous && d.ycontig && d.N % 2 == 0 && d.io != KRON_R64F) {
+        kron_status r = KRON_ERR_NOT_SUPPORTED;
+        switch (d.io) {
+            case KRON_R32F: r = d.D == 2 ? launch_pair_f32_d2(d, st) : launch_pair_f32_d3(d, st); break;
+            case KRON_R16BF: r = d.D == 2 ? launch_pair_bf16_d2(d, st) : launch_pair_bf16_d3(d, st); break;
+            case KRON_R16F: r = d.D == 2 ? launch_pair_f16_d2(d, st) : launch_pair_f16_d3(d, st); break;
+            default: break;
+        }
+        if (r != KRON_ERR_NOT_SUPPORTED) return r;
+    }
     switch (d.io) {
         case KRON_R32F: return d.D == 2 ? launch_fiber_f32_d2(d, st) : launch_fiber_f32_d3(d, st);
         case KRON_R64F: return d.D == 2 ? launch_fiber_f64_d2(d, st) : launch_fiber_f64_d3(d, st);
@@ -189,6 +199,7 @@ KRON_API kron_status kron2_batched(kron_stream_t stream, char transa, char trans
     const int N = d.N;
     d.contiguous = ma == N && na == N && mb == N && nb == N && !tx && ldx == N && ldxp == (int64_t)N * N &&
                    ((uintptr_t)X) % 16 == 0;
+    d.ycontig = d.contiguous && ldy == N && ldyp == (int64_t)N * N && ((uintptr_t)Y) % 16 == 0;
     choose_yvec(d);
     return dispatch(d, (cudaStream_t)stream);
 }
@@ -248,6 +259,7 @@ KRON_API kron_status kron3_batched(kron_stream_t stream, char transa, char trans
     const int N = d.N;
     d.contiguous = ma == N && na == N && mb == N && nb == N && mc == N && nc == N && ldx == N &&
                    ldx2 == N * N && ldxp == (int64_t)N * N * N && ((uintptr_t)X) % 16 == 0;
+    d.ycontig = d.contiguous && ldy == N && ldy2 == N * N && ldyp == (int64_t)N * N * N && ((uintptr_t)Y) % 16 == 0;
     choose_yvec(d);
     return dispatch(d, (cudaStream_t)stream);
 }

@@ -33,6 +33,7 @@ struct KronDesc {
     kron_compute comp = KRON_COMPUTE_NATIVE;
     // derived by the dispatcher
     int contiguous = 0;  // square, minimal leading dims, 16-B aligned X: bulk-copy tiles
+    int ycontig = 0;     // square, minimal leading dims, 16-B aligned Y
     int yvec = 0;        // Y fiber store chunk in bytes (0 = element stores)
     // launch configuration (0 = choose automatically)
     int P = 0;           // instances per tile
@@ -55,6 +56,15 @@ kron_status launch_fiber_bf16_d2(const KronDesc& d, cudaStream_t s);
 kron_status launch_fiber_bf16_d3(const KronDesc& d, cudaStream_t s);
 kron_status launch_fiber_f16_d2(const KronDesc& d, cudaStream_t s);
 kron_status launch_fiber_f16_d3(const KronDesc& d, cudaStream_t s);
+
+// Packed-pair FP32 kernels (even N, contiguous X and Y); KRON_ERR_NOT_SUPPORTED
+// for shapes they do not handle.
+kron_status launch_pair_f32_d2(const KronDesc& d, cudaStream_t s);
+kron_status launch_pair_f32_d3(const KronDesc& d, cudaStream_t s);
+kron_status launch_pair_bf16_d2(const KronDesc& d, cudaStream_t s);
+kron_status launch_pair_bf16_d3(const KronDesc& d, cudaStream_t s);
+kron_status launch_pair_f16_d2(const KronDesc& d, cudaStream_t s);
+kron_status launch_pair_f16_d3(const KronDesc& d, cudaStream_t s);
 
 // Tensor-core split-precision kernels (R32F or R16BF storage).
 kron_status launch_tc(const KronDesc& d, cudaStream_t s);

@@ -1,0 +1,6 @@
+// Instantiates the packed-pair FP32 kernels for __half storage, 2-D operands.
+#include "kron_pair.cuh"
+
+namespace kron {
+kron_status launch_pair_f16_d2(const KronDesc& d, cudaStream_t s) { return launch_pair_d<__half, 2>(d, s); }
+}  // namespace kron
