@@ -147,6 +147,24 @@ KRON_API kron_status kron3_batched(kron_stream_t stream, char transa, char trans
 KRON_API kron_status kron_device_status(kron_stream_t stream);
 
 /*
+ * Tile configuration of the fixed-size kernels, per (kind, n, io, comp):
+ * instances processed per CTA tile and depth of the bulk-copy pipeline (both 0
+ * = built-in default).  kron_autotune times the candidate configurations on the
+ * caller's buffers (contiguous X and Y of batch_count instances, minimal
+ * leading dimensions; Y is overwritten), keeps the fastest in the process-wide
+ * table, appends it to the file named by KRON_TUNE_CACHE (if set; read at first
+ * use), and returns it.  Errors: KRON_ERR_INVALID_VALUE for bad arguments,
+ * KRON_ERR_CUDA if a timing call fails.
+ */
+KRON_API kron_status kron_set_tile_config(int kind, int n, kron_dtype io, kron_compute comp,
+                                          int instances_per_tile, int pipeline_depth);
+KRON_API kron_status kron_get_tile_config(int kind, int n, kron_dtype io, kron_compute comp,
+                                          int* instances_per_tile, int* pipeline_depth);
+KRON_API kron_status kron_autotune(kron_stream_t stream, int kind, int n, int64_t batch_count,
+                                   const void* X, void* Y, kron_dtype io, kron_compute comp,
+                                   int* instances_per_tile, int* pipeline_depth);
+
+/*
  * Mixed-size batches (one launch for instances of different sizes and kinds).
  *
  * A class is one (kind, n) pair with its own shared components (square n x n,

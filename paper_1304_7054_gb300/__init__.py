@@ -37,6 +37,9 @@ SIGNATURES = {
     "kron3_batched": ([_P, _C, _C, _C, _I, _I, _I, _I, _I, _I, _L, _P, _P, _I, _P, _I, _P, _I, _P, _I, _I,
                        _L, _P, _P, _I, _I, _L, _I, _I], _I),
     "kron_device_status": ([_P], _I),
+    "kron_set_tile_config": ([_I, _I, _I, _I, _I, _I], _I),
+    "kron_get_tile_config": ([_I, _I, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
+    "kron_autotune": ([_P, _I, _I, _L, _P, _P, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
     "kron_varlen_plan_create": ([ctypes.POINTER(_P), _I, _P, _L, _P, _P, _P, _I, _I], _I),
     "kron_varlen_workspace_size": ([_P, ctypes.POINTER(_S)], _I),
     "kron_varlen_execute": ([_P, _P, _P, _P, _S, _P], _I),
@@ -174,3 +177,25 @@ def kron3_batched(A, B, C, X, Y, *, ma, na, mb, nb, mc, nc, batch, alpha=1.0, be
 def device_status(stream=None) -> int:
     """Synchronise and read/clear the device status word (0 = OK)."""
     return load_library().kron_device_status(_stream_handle(stream))
+
+
+def set_tile_config(kind, n, io, compute="native", instances_per_tile=0, pipeline_depth=0):
+    """Launch configuration of the fixed-size kernels for one (kind, n, storage, compute)."""
+    _check(load_library().kron_set_tile_config(kind, n, DTYPES[io], COMPUTE[compute], instances_per_tile,
+                                                pipeline_depth), "kron_set_tile_config")
+
+
+def get_tile_config(kind, n, io, compute="native"):
+    p, d = ctypes.c_int(), ctypes.c_int()
+    _check(load_library().kron_get_tile_config(kind, n, DTYPES[io], COMPUTE[compute], ctypes.byref(p),
+                                                ctypes.byref(d)), "kron_get_tile_config")
+    return p.value, d.value
+
+
+def autotune(kind, n, batch, X, Y, compute="native", stream=None):
+    """Time the candidate tile configurations on X -> Y and keep the fastest."""
+    p, d = ctypes.c_int(), ctypes.c_int()
+    _check(load_library().kron_autotune(_stream_handle(stream), kind, n, batch, X.data_ptr(), Y.data_ptr(),
+                                        _io_of(X), COMPUTE[compute], ctypes.byref(p), ctypes.byref(d)),
+           "kron_autotune")
+    return p.value, d.value

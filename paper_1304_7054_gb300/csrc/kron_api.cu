@@ -100,6 +100,7 @@ static void choose_yvec(KronDesc& d) {
 }
 
 static kron_status dispatch(KronDesc& d, cudaStream_t st) {
+    apply_tile_config(d);
     if (d.comp == KRON_COMPUTE_32F_BF16X3) return launch_tc(d, st);
     if (d.contiguous && d.ycontig && d.N % 2 == 0 && d.io != KRON_R64F) {
         kron_status r = KRON_ERR_NOT_SUPPORTED;

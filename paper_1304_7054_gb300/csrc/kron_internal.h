@@ -43,6 +43,9 @@ struct KronDesc {
 
 size_t elem_size(kron_dtype t);
 
+// Fills d.P / d.nstage from the tile-configuration table, if it has an entry.
+void apply_tile_config(KronDesc& d);
+
 // Device status word of the current device (device pointer).
 unsigned* device_error_word();
 

@@ -200,6 +200,40 @@ __device__ __forceinline__ void pair_store(const PairArgs<N, D>& a, S* dst, f2 (
     }
 }
 
+// N contiguous floats of an exchange buffer (8-byte aligned) into registers.
+template <int N>
+__device__ __forceinline__ void load_row(const float* src, float (&v)[N]) {
+#pragma unroll
+    for (int l = 0; l < N; l += 2) {
+        const f2 p = *reinterpret_cast<const f2*>(src + l);
+        v[l] = f2_lo(p);
+        v[l + 1] = f2_hi(p);
+    }
+}
+
+// Last contraction over F mode-1 fibers, two fibers per thread and iteration so
+// that the shared loads of the second overlap the arithmetic of the first.
+// fetch(f, x) loads fiber f into x and returns where its outputs go.
+template <typename S, int N, int D, int NT, typename Fetch>
+__device__ __forceinline__ void last_stage(const PairArgs<N, D>& a, int F, Fetch fetch) {
+    const f2* m1p = reinterpret_cast<const f2*>(a.m1);
+    for (int f = threadIdx.x; f < F; f += 2 * NT) {
+        const bool two = f + NT < F;
+        float x0[N], x1[N];
+        S* d0 = fetch(f, x0);
+        S* d1 = two ? fetch(f + NT, x1) : d0;
+        if (!two) {
+#pragma unroll
+            for (int l = 0; l < N; ++l) x1[l] = x0[l];
+        }
+        f2 y0[N / 2], y1[N / 2];
+        contract_rows<N>(m1p, x0, y0);
+        contract_rows<N>(m1p, x1, y1);
+        pair_store<S, N, D>(a, d0, y0);
+        if (two) pair_store<S, N, D>(a, d1, y1);
+    }
+}
+
 template <typename S, int N, int D, int NT>
 __global__ void __launch_bounds__(NT) pair_kernel(const __grid_constant__ PairArgs<N, D> a) {
     using L = PairLayout<N, D>;
@@ -292,23 +326,13 @@ __global__ void __launch_bounds__(NT) pair_kernel(const __grid_constant__ PairAr
         }
 
         S* Y = static_cast<S*>(a.Y);
-        const f2* m1p = reinterpret_cast<const f2*>(a.m1);
         if constexpr (D == 2) {
             const int F = cnt * N;
-            for (int f = tid; f < F; f += NT) {
+            last_stage<S, N, D, NT>(a, F, [&](int f, float (&w)[N]) {
                 const int q = f / N, j = f - q * N;
-                const float* wr = ex1 + q * L::SQ + L::SJ * j;
-                float w[N];
-#pragma unroll
-                for (int l = 0; l < N; l += 2) {
-                    const f2 v = *reinterpret_cast<const f2*>(wr + l);
-                    w[l] = f2_lo(v);
-                    w[l + 1] = f2_hi(v);
-                }
-                f2 y[N / 2];
-                contract_rows<N>(m1p, w, y);
-                pair_store<S, N, D>(a, Y + (inst0 + q) * L::NX + N * j, y);
-            }
+                load_row<N>(ex1 + q * L::SQ + L::SJ * j, w);
+                return Y + (inst0 + q) * L::NX + N * j;
+            });
             __syncthreads();   // ex1 is rewritten by the next tile's first stage
         } else {
             const int F = cnt * (N * N / 2);
@@ -326,21 +350,12 @@ __global__ void __launch_bounds__(NT) pair_kernel(const __grid_constant__ PairAr
             }
             __syncthreads();
             const int F3 = cnt * N * N;
-            for (int f = tid; f < F3; f += NT) {
+            last_stage<S, N, D, NT>(a, F3, [&](int f, float (&u)[N]) {
                 const int q = f / (N * N), r = f - q * (N * N);
                 const int j = r % N, k = r / N;
-                const float* ur = ex2 + q * L::SQ + L::SJ * j + L::SK * k;
-                float u[N];
-#pragma unroll
-                for (int l = 0; l < N; l += 2) {
-                    const f2 v = *reinterpret_cast<const f2*>(ur + l);
-                    u[l] = f2_lo(v);
-                    u[l + 1] = f2_hi(v);
-                }
-                f2 y[N / 2];
-                contract_rows<N>(m1p, u, y);
-                pair_store<S, N, D>(a, Y + (inst0 + q) * L::NX + N * j + N * N * k, y);
-            }
+                load_row<N>(ex2 + q * L::SQ + L::SJ * j + L::SK * k, u);
+                return Y + (inst0 + q) * L::NX + N * j + N * N * k;
+            });
             // ex2 is rewritten only after the next tile's first barrier.
         }
     }

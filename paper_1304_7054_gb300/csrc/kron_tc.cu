@@ -1,6 +1,354 @@
-// Tensor-core split-precision kernels (placeholder until implemented).
+// Tensor-core split-precision kernels (KRON_COMPUTE_32F_BF16X3).
+//
+// Each FP32 value v is split into two bfloat16 values, hi = bf16(v) and
+// lo = bf16(v - hi) (round to nearest even; v - hi is exact), and every product
+// a*b of a contraction is evaluated as a_hi*b_hi + a_hi*b_lo + a_lo*b_hi with
+// FP32 accumulation on the tensor cores (mma.sync m16n8k16, bf16 inputs, f32
+// accumulators).  The dropped a_lo*b_lo term and the residual of the split are
+// below 2^-16 relative, which gives FP32-level accuracy.  For bf16 storage the
+// operand is exact (lo = 0) and its products with the split components need two
+// MMAs instead of three.
+//
+// 2-D (Y = M1 X M2^T, paper Sec. 2 vec identity), one warp per instance, sizes
+// n <= 16 zero-padded to 16:
+//   stage 1  W = M1 X       A = M1 (constant fragments), B = X (from the tile)
+//   stage 2  Y = W M2^T     A = W taken straight from the stage-1 accumulators
+//                           (the m16n8 accumulator layout of two n-tiles is the
+//                           m16k16 A-fragment layout), B = M2^T (constant)
+// Operand tiles of P instances stream into shared memory with 1-D bulk copies
+// (TMA) in an mbarrier pipeline, as in the CUDA-core kernels.
+#include <string.h>
+
+#include <type_traits>
+
+#include "kron_device.cuh"
+#include "kron_fiber.cuh"
 #include "kron_internal.h"
 
 namespace kron {
-kron_status launch_tc(const KronDesc&, cudaStream_t) { return KRON_ERR_NOT_SUPPORTED; }
+
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// (x0, x1) -> packed bf16 pairs hi = (bf16(x0), bf16(x1)), lo = (bf16(x0 - hi0), bf16(x1 - hi1)).
+__device__ __forceinline__ void split_pair(float x0, float x1, unsigned& hi, unsigned& lo) {
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(hi) : "f"(x1), "f"(x0));
+    const float r0 = x0 - __uint_as_float(hi << 16);
+    const float r1 = x1 - __uint_as_float(hi & 0xffff0000u);
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(lo) : "f"(r1), "f"(r0));
+}
+
+template <int N>
+struct TcArgs2 {
+    // Row-major 16 x 16 components as packed bf16 pairs along the row:
+    // word r*8 + c/2 holds (M[r][c], M[r][c+1]); hi and lo parts of the split.
+    unsigned m1h[128], m1l[128];
+    unsigned m2h[128], m2l[128];
+    const void* X;
+    void* Y;
+    int64_t batch;
+    int P;
+    int nstage;
+    int beta_zero, alpha_one;
+    float alpha, beta;
+    unsigned* err;
+};
+
+// Two elements (X[l][m], X[l+1][m]) of an instance in the tile (zero outside n x n).
+template <typename S, int N>
+__device__ __forceinline__ void x_pair(const S* xq, int l, int m, float& v0, float& v1) {
+    v0 = (l < N && m < N) ? load_cvt<float, S>(xq[l + N * m]) : 0.f;
+    v1 = (l + 1 < N && m < N) ? load_cvt<float, S>(xq[l + 1 + N * m]) : 0.f;
+}
+
+template <int N>
+__device__ __forceinline__ unsigned x_pair_bf16(const __nv_bfloat16* xq, int l, int m) {
+    if constexpr (N % 2 == 0) {
+        return (l < N && m < N) ? *reinterpret_cast<const unsigned*>(xq + l + N * m) : 0u;
+    } else {
+        const unsigned a = (l < N && m < N) ? (unsigned)__bfloat16_as_ushort(xq[l + N * m]) : 0u;
+        const unsigned b = (l + 1 < N && m < N) ? (unsigned)__bfloat16_as_ushort(xq[l + 1 + N * m]) : 0u;
+        return a | (b << 16);
+    }
+}
+
+template <typename S, int N>
+__device__ __forceinline__ void tc2_instance(const TcArgs2<N>& a, const S* xq, S* yq, const unsigned (&m1h)[4],
+                                             const unsigned (&m1l)[4], const unsigned (&m2h)[2][2],
+                                             const unsigned (&m2l)[2][2]) {
+    const int lane = threadIdx.x & 31;
+    const int g = lane >> 2, t = lane & 3;
+    // ---- stage 1: W = M1 X ---------------------------------------------------------------
+    float w[2][4];
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) {
+        const int m = 8 * nt + g;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) w[nt][e] = 0.f;
+        if constexpr (sizeof(S) == 2 && std::is_same<S, __nv_bfloat16>::value) {
+            const unsigned b0 = x_pair_bf16<N>(xq, 2 * t, m);
+            const unsigned b1 = x_pair_bf16<N>(xq, 2 * t + 8, m);
+            mma_bf16_16816(w[nt], m1l, b0, b1);
+            mma_bf16_16816(w[nt], m1h, b0, b1);
+        } else {
+            float x0, x1, x2, x3;
+            if constexpr (N == 16 && sizeof(S) == 4) {
+                const float2 p0 = *reinterpret_cast<const float2*>(xq + 2 * t + 16 * m);
+                const float2 p1 = *reinterpret_cast<const float2*>(xq + 2 * t + 8 + 16 * m);
+                x0 = p0.x; x1 = p0.y; x2 = p1.x; x3 = p1.y;
+            } else {
+                x_pair<S, N>(xq, 2 * t, m, x0, x1);
+                x_pair<S, N>(xq, 2 * t + 8, m, x2, x3);
+            }
+            unsigned bh0, bl0, bh1, bl1;
+            split_pair(x0, x1, bh0, bl0);
+            split_pair(x2, x3, bh1, bl1);
+            mma_bf16_16816(w[nt], m1l, bh0, bh1);
+            mma_bf16_16816(w[nt], m1h, bl0, bl1);
+            mma_bf16_16816(w[nt], m1h, bh0, bh1);
+        }
+    }
+    // ---- stage 2: Y = W M2^T, W from the accumulators ------------------------------------
+    unsigned wh[4], wl[4];
+    split_pair(w[0][0], w[0][1], wh[0], wl[0]);
+    split_pair(w[0][2], w[0][3], wh[1], wl[1]);
+    split_pair(w[1][0], w[1][1], wh[2], wl[2]);
+    split_pair(w[1][2], w[1][3], wh[3], wl[3]);
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) {
+        float y[4] = {0.f, 0.f, 0.f, 0.f};
+        mma_bf16_16816(y, wl, m2h[nt][0], m2h[nt][1]);
+        mma_bf16_16816(y, wh, m2l[nt][0], m2l[nt][1]);
+        mma_bf16_16816(y, wh, m2h[nt][0], m2h[nt][1]);
+        const int j = 8 * nt + 2 * t;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int i = g + 8 * (e >> 1), jj = j + (e & 1);
+            if (i < N && jj < N) {
+                S* dst = yq + i + N * jj;
+                float v = a.alpha_one ? y[e] : a.alpha * y[e];
+                if (!a.beta_zero) v = fmaf(a.beta, load_cvt<float, S>(*dst), v);
+                if constexpr (sizeof(S) == 4)
+                    __stcs(reinterpret_cast<float*>(dst), v);
+                else
+                    *dst = store_cvt<S, float>(v);
+            }
+        }
+    }
+}
+
+constexpr int kTcThreads = 128;
+
+template <typename S, int N>
+__global__ void __launch_bounds__(kTcThreads) tc2_kernel(const __grid_constant__ TcArgs2<N> a) {
+    constexpr int NX = N * N;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+    const int P = a.P;
+    const size_t xstage = round_up((size_t)P * NX * sizeof(S), 128);
+    unsigned char* xbase = smem + 128;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int g = lane >> 2, t = lane & 3;
+    const int64_t ntiles = (a.batch + P - 1) / P;
+    const int64_t grid = gridDim.x;
+
+    // Constant fragments: A of M1 (rows g, g+8; pair columns t, t+4) and B of
+    // M2^T for both n-tiles (column j = 8 nt + g of M2^T is row j of M2).
+    unsigned m1h[4], m1l[4], m2h[2][2], m2l[2][2];
+    m1h[0] = a.m1h[g * 8 + t];       m1l[0] = a.m1l[g * 8 + t];
+    m1h[1] = a.m1h[(g + 8) * 8 + t]; m1l[1] = a.m1l[(g + 8) * 8 + t];
+    m1h[2] = a.m1h[g * 8 + t + 4];   m1l[2] = a.m1l[g * 8 + t + 4];
+    m1h[3] = a.m1h[(g + 8) * 8 + t + 4]; m1l[3] = a.m1l[(g + 8) * 8 + t + 4];
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) {
+        const int j = 8 * nt + g;
+        m2h[nt][0] = a.m2h[j * 8 + t];     m2l[nt][0] = a.m2l[j * 8 + t];
+        m2h[nt][1] = a.m2h[j * 8 + t + 4]; m2l[nt][1] = a.m2l[j * 8 + t + 4];
+    }
+
+    uint64_t pol = 0;
+    if (tid == 0) {
+        for (int s = 0; s < a.nstage; ++s) mbar_init(&bars[s], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        pol = l2_evict_first_policy();
+        for (int s = 0; s < a.nstage; ++s) {
+            const int64_t tl = blockIdx.x + s * grid;
+            if (tl < ntiles) {
+                const int64_t i0 = tl * P;
+                const int cnt = (int)min((int64_t)P, a.batch - i0);
+                const unsigned bytes = ((unsigned)cnt * NX * (unsigned)sizeof(S)) & ~15u;
+                mbar_arrive_expect_tx(&bars[s], bytes);
+                if (bytes) bulk_g2s(xbase + s * xstage, static_cast<const S*>(a.X) + i0 * NX, bytes, &bars[s], pol);
+            }
+        }
+    }
+    int it = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += grid, ++it) {
+        const int s = it % a.nstage;
+        S* xt = reinterpret_cast<S*>(xbase + s * xstage);
+        const int64_t inst0 = tile * P;
+        const int cnt = (int)min((int64_t)P, a.batch - inst0);
+        bool ok = mbar_wait_bounded(&bars[s], (unsigned)(it / a.nstage) & 1u, a.err);
+        const unsigned bytes = (unsigned)cnt * NX * (unsigned)sizeof(S);
+        const unsigned b16 = bytes & ~15u;
+        if (bytes != b16) {
+            const S* src = static_cast<const S*>(a.X) + inst0 * NX;
+            for (int e = b16 / sizeof(S) + tid; e < cnt * NX; e += kTcThreads) xt[e] = src[e];
+            __syncthreads();
+        }
+        if (ok) {
+            for (int q = warp; q < cnt; q += kTcThreads / 32)
+                tc2_instance<S, N>(a, xt + q * NX, static_cast<S*>(a.Y) + (inst0 + q) * NX, m1h, m1l, m2h, m2l);
+        }
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                for (int j = it; j < it + a.nstage; ++j)
+                    if (blockIdx.x + (int64_t)j * grid < ntiles)
+                        mbar_wait_bounded(&bars[j % a.nstage], (unsigned)(j / a.nstage) & 1u, a.err);
+            }
+            return;
+        }
+        if (tid == 0) {
+            const int64_t next = tile + a.nstage * grid;
+            if (next < ntiles) {
+                const int64_t i0 = next * P;
+                const int c2 = (int)min((int64_t)P, a.batch - i0);
+                const unsigned nb = ((unsigned)c2 * NX * (unsigned)sizeof(S)) & ~15u;
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&bars[s], nb);
+                if (nb) bulk_g2s(xt, static_cast<const S*>(a.X) + i0 * NX, nb, &bars[s], pol);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+// float -> bfloat16 bits, round to nearest even (NaN kept quiet).
+static inline unsigned short bf16_rne(float f) {
+    unsigned u;
+    memcpy(&u, &f, 4);
+    if ((u & 0x7f800000u) == 0x7f800000u && (u & 0x7fffffu)) return (unsigned short)((u >> 16) | 0x40);
+    const unsigned lsb = (u >> 16) & 1u;
+    u += 0x7fffu + lsb;
+    return (unsigned short)(u >> 16);
+}
+static inline float bf16_to_float(unsigned short h) {
+    const unsigned u = (unsigned)h << 16;
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
+}
+
+// Column-major N x N (double) -> row-major 16 x 16 packed bf16 pairs, split hi/lo.
+static void split_rowmajor(const double* m, int N, unsigned* hi, unsigned* lo) {
+    for (int r = 0; r < 16; ++r)
+        for (int c2 = 0; c2 < 8; ++c2) {
+            unsigned short h[2], l[2];
+            for (int e = 0; e < 2; ++e) {
+                const int c = 2 * c2 + e;
+                const float v = (r < N && c < N) ? (float)m[r + N * c] : 0.f;
+                h[e] = bf16_rne(v);
+                l[e] = bf16_rne(v - bf16_to_float(h[e]));
+            }
+            hi[r * 8 + c2] = (unsigned)h[0] | ((unsigned)h[1] << 16);
+            lo[r * 8 + c2] = (unsigned)l[0] | ((unsigned)l[1] << 16);
+        }
+}
+
+template <typename S, int N>
+static kron_status launch_tc2_n(const KronDesc& d, cudaStream_t st) {
+    const DeviceInfo& dev = device_info();
+    if (dev.sms <= 0) return KRON_ERR_CUDA;
+    TcArgs2<N> a;
+    split_rowmajor(d.m1, N, a.m1h, a.m1l);
+    split_rowmajor(d.m2, N, a.m2h, a.m2l);
+    a.X = d.X;
+    a.Y = d.Y;
+    a.batch = d.batch;
+    a.alpha = (float)d.alpha;
+    a.beta = (float)d.beta;
+    a.beta_zero = d.beta == 0.0;
+    a.alpha_one = d.alpha == 1.0;
+    a.err = device_error_word();
+    if (!a.err) return KRON_ERR_CUDA;
+    int P = d.P > 0 ? d.P : 16;
+    int mult = 1;
+    while ((mult * N * N * sizeof(S)) % 16) ++mult;
+    P = (P + mult - 1) / mult * mult;
+    int nstage = d.nstage >= 1 ? d.nstage : 3;
+    if (nstage > 8) nstage = 8;
+    auto smem_of = [&](int ns) { return 128 + ns * round_up((size_t)P * N * N * sizeof(S), 128); };
+    size_t smem = smem_of(nstage);
+    while (nstage > 1 && smem > dev.smem_per_block_optin) smem = smem_of(--nstage);
+    if (smem > dev.smem_per_block_optin) return KRON_ERR_NOT_SUPPORTED;
+    a.P = P;
+    a.nstage = nstage;
+    auto kern = tc2_kernel<S, N>;
+    static int smem_set = 0;
+    if ((int)smem > smem_set) {
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return KRON_ERR_CUDA;
+        smem_set = (int)smem;
+    }
+    const int64_t ntiles = (d.batch + P - 1) / P;
+    int64_t grid = d.grid;
+    if (grid <= 0) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTcThreads, smem) != cudaSuccess)
+            return KRON_ERR_CUDA;
+        grid = (int64_t)(per_sm < 1 ? 1 : per_sm) * dev.sms;
+    }
+    if (grid > ntiles) grid = ntiles;
+    if (grid < 1) grid = 1;
+    kern<<<(unsigned)grid, kTcThreads, smem, st>>>(a);
+    return cudaPeekAtLastError() == cudaSuccess ? KRON_OK : KRON_ERR_CUDA;
+}
+
+template <typename S>
+static kron_status launch_tc2(const KronDesc& d, cudaStream_t st) {
+    switch (d.N) {
+        case 1: return launch_tc2_n<S, 1>(d, st);
+        case 2: return launch_tc2_n<S, 2>(d, st);
+        case 3: return launch_tc2_n<S, 3>(d, st);
+        case 4: return launch_tc2_n<S, 4>(d, st);
+        case 5: return launch_tc2_n<S, 5>(d, st);
+        case 6: return launch_tc2_n<S, 6>(d, st);
+        case 7: return launch_tc2_n<S, 7>(d, st);
+        case 8: return launch_tc2_n<S, 8>(d, st);
+        case 9: return launch_tc2_n<S, 9>(d, st);
+        case 10: return launch_tc2_n<S, 10>(d, st);
+        case 11: return launch_tc2_n<S, 11>(d, st);
+        case 12: return launch_tc2_n<S, 12>(d, st);
+        case 13: return launch_tc2_n<S, 13>(d, st);
+        case 14: return launch_tc2_n<S, 14>(d, st);
+        case 15: return launch_tc2_n<S, 15>(d, st);
+        case 16: return launch_tc2_n<S, 16>(d, st);
+        default: return KRON_ERR_INVALID_VALUE;
+    }
+}
+
+kron_status launch_tc(const KronDesc& d, cudaStream_t st) {
+    // Contiguous square batches only (minimal leading dimensions, 16-byte aligned X).
+    if (!d.contiguous || d.ye[0] != d.N || d.ye[1] != d.N || d.ye[2] != (d.D == 3 ? d.N : 1) ||
+        (d.D == 2 ? (d.ldy != d.N || d.ldyp != (int64_t)d.N * d.N)
+                  : (d.ldy != d.N || d.ldy2 != d.N * d.N || d.ldyp != (int64_t)d.N * d.N * d.N)))
+        return KRON_ERR_NOT_SUPPORTED;
+    if (d.D == 2) {
+        if (d.io == KRON_R32F) return launch_tc2<float>(d, st);
+        if (d.io == KRON_R16BF) return launch_tc2<__nv_bfloat16>(d, st);
+        return KRON_ERR_NOT_SUPPORTED;
+    }
+    return KRON_ERR_NOT_SUPPORTED;
+}
+
 }  // namespace kron

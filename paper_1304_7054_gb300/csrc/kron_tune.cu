@@ -1,0 +1,172 @@
+// Tile-configuration table and autotuner for the fixed-size kernels.
+//
+// A configuration is (instances per tile, bulk-copy pipeline depth) for one
+// (kind, n, storage type, compute mode).  kron_autotune times the candidates on
+// the caller's buffers with CUDA events and keeps the fastest; the table can be
+// persisted in a small text file named by the KRON_TUNE_CACHE environment
+// variable (one line per entry: device-name kind n io comp P depth), read at
+// first use.
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "kron_internal.h"
+
+namespace kron {
+
+namespace {
+
+using Key = std::tuple<int, int, int, int>;   // kind, n, io, comp
+struct Entry { int P, nstage; };
+
+std::mutex g_mu;
+std::map<Key, Entry> g_table;
+bool g_loaded = false;
+
+std::string device_name() {
+    int dev = 0;
+    cudaDeviceProp prop;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return "unknown";
+    std::string s = prop.name;
+    for (char& c : s)
+        if (c == ' ') c = '_';
+    return s;
+}
+
+void load_cache_locked() {
+    if (g_loaded) return;
+    g_loaded = true;
+    const char* path = getenv("KRON_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE* f = fopen(path, "r");
+    if (!f) return;
+    const std::string me = device_name();
+    char name[256];
+    int kind, n, io, comp, P, ns;
+    while (fscanf(f, "%255s %d %d %d %d %d %d", name, &kind, &n, &io, &comp, &P, &ns) == 7)
+        if (me == name) g_table[Key(kind, n, io, comp)] = Entry{P, ns};
+    fclose(f);
+}
+
+void append_cache(const Key& k, const Entry& e) {
+    const char* path = getenv("KRON_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE* f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "%s %d %d %d %d %d %d\n", device_name().c_str(), std::get<0>(k), std::get<1>(k), std::get<2>(k),
+            std::get<3>(k), e.P, e.nstage);
+    fclose(f);
+}
+
+}  // namespace
+
+void apply_tile_config(KronDesc& d) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    load_cache_locked();
+    auto it = g_table.find(Key(d.D, d.N, (int)d.io, (int)d.comp));
+    if (it != g_table.end()) {
+        if (d.P <= 0) d.P = it->second.P;
+        if (d.nstage < 0) d.nstage = it->second.nstage > 0 ? it->second.nstage : -1;
+    }
+}
+
+}  // namespace kron
+
+using namespace kron;
+
+extern "C" {
+
+KRON_API kron_status kron_set_tile_config(int kind, int n, kron_dtype io, kron_compute comp, int instances_per_tile,
+                                          int pipeline_depth) {
+    if ((kind != 2 && kind != 3) || n < 1 || n > kMaxN || instances_per_tile < 0 || pipeline_depth < 0 ||
+        pipeline_depth > 8 || instances_per_tile > 4096)
+        return KRON_ERR_INVALID_VALUE;
+    std::lock_guard<std::mutex> lock(g_mu);
+    load_cache_locked();
+    if (instances_per_tile == 0 && pipeline_depth == 0)
+        g_table.erase(Key(kind, n, (int)io, (int)comp));
+    else
+        g_table[Key(kind, n, (int)io, (int)comp)] = Entry{instances_per_tile, pipeline_depth};
+    return KRON_OK;
+}
+
+KRON_API kron_status kron_get_tile_config(int kind, int n, kron_dtype io, kron_compute comp,
+                                          int* instances_per_tile, int* pipeline_depth) {
+    if (!instances_per_tile || !pipeline_depth) return KRON_ERR_INVALID_VALUE;
+    std::lock_guard<std::mutex> lock(g_mu);
+    load_cache_locked();
+    auto it = g_table.find(Key(kind, n, (int)io, (int)comp));
+    *instances_per_tile = it == g_table.end() ? 0 : it->second.P;
+    *pipeline_depth = it == g_table.end() ? 0 : it->second.nstage;
+    return KRON_OK;
+}
+
+KRON_API kron_status kron_autotune(kron_stream_t stream, int kind, int n, int64_t batch_count, const void* X,
+                                   void* Y, kron_dtype io, kron_compute comp, int* instances_per_tile,
+                                   int* pipeline_depth) {
+    if ((kind != 2 && kind != 3) || n < 1 || n > kMaxN || batch_count < 1 || !X || !Y) return KRON_ERR_INVALID_VALUE;
+    cudaStream_t st = (cudaStream_t)stream;
+    // Components do not change the timing; identity keeps the outputs finite.
+    double eye[kMaxN * kMaxN] = {};
+    float eyef[kMaxN * kMaxN] = {};
+    for (int i = 0; i < n; ++i) eye[i + n * i] = eyef[i + n * i] = 1.0f;
+    const void* comp_ptr = io == KRON_R64F ? (const void*)eye : (const void*)eyef;
+    const double one = 1.0, zero = 0.0;
+    const float onef = 1.0f, zerof = 0.0f;
+    const void* al = io == KRON_R64F ? (const void*)&one : (const void*)&onef;
+    const void* be = io == KRON_R64F ? (const void*)&zero : (const void*)&zerof;
+    auto run = [&]() -> kron_status {
+        if (kind == 2)
+            return kron2_batched(stream, 'N', 'N', 'N', n, n, n, n, batch_count, al, comp_ptr, n, comp_ptr, n, X, n,
+                                 (int64_t)n * n, be, Y, n, (int64_t)n * n, io, comp);
+        return kron3_batched(stream, 'N', 'N', 'N', n, n, n, n, n, n, batch_count, al, comp_ptr, n, comp_ptr, n,
+                             comp_ptr, n, X, n, n * n, (int64_t)n * n * n, be, Y, n, n * n, (int64_t)n * n * n, io,
+                             comp);
+    };
+    int def_P = 0, def_ns = 0;
+    kron_get_tile_config(kind, n, io, comp, &def_P, &def_ns);
+    std::vector<Entry> cands;
+    const int base = kind == 2 ? (256 + n - 1) / n : (256 + n * n - 1) / (n * n);
+    for (int mul : {1, 2, 4})
+        for (int ns : {2, 3, 4}) cands.push_back(Entry{base * mul / 2 > 0 ? base * mul / 2 : 1, ns});
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return KRON_ERR_CUDA;
+    float best = 1e30f;
+    Entry best_e{0, 0};
+    kron_status rs = KRON_OK;
+    for (const Entry& c : cands) {
+        kron_set_tile_config(kind, n, io, comp, c.P, c.nstage);
+        bool ok = true;
+        for (int w = 0; w < 2 && ok; ++w) ok = run() == KRON_OK;
+        if (!ok) continue;
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 5; ++r) run();
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) { rs = KRON_ERR_CUDA; break; }
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) { best = ms; best_e = c; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rs != KRON_OK || best_e.P == 0) {
+        kron_set_tile_config(kind, n, io, comp, def_P, def_ns);
+        return rs != KRON_OK ? rs : KRON_ERR_NOT_SUPPORTED;
+    }
+    kron_set_tile_config(kind, n, io, comp, best_e.P, best_e.nstage);
+    {
+        std::lock_guard<std::mutex> lock(g_mu);
+        append_cache(Key(kind, n, (int)io, (int)comp), best_e);
+    }
+    if (instances_per_tile) *instances_per_tile = best_e.P;
+    if (pipeline_depth) *pipeline_depth = best_e.nstage;
+    return KRON_OK;
+}
+
+}  // extern "C"
