@@ -231,6 +231,238 @@ __global__ void __launch_bounds__(kTcThreads) tc2_kernel(const __grid_constant__
 }
 
 // ---------------------------------------------------------------------------
+// 3-D: one warp per instance, three tensor-core contractions.
+//
+//   per plane p (modes 1 and 2), two planes at a time for instruction-level
+//   parallelism:
+//     stage 1  W' = M2 X_p^T      A = M2 (constant), B = X_p^T read from the
+//                                 FP32 instance in shared memory and split
+//     stage 2  T_p^T = W' M1^T    A = W' from the accumulators, B = M1^T (constant)
+//              T_p^T is split and stored as row p of the matrix T[p][r],
+//              r = i + 16 j (hi half and lo half, 512 bytes each); for n = 16
+//              row p overwrites the FP32 plane p it was computed from
+//   stage 3 (mode 3), per 16 rows r:  Y[r][k] = sum_p T[p][r] M3[k][p]
+//              A via ldmatrix.trans of T, B = M3^T (constant); rows r = i + 16 j
+//              make consecutive lanes write consecutive elements of Y.
+// The intermediates never leave shared memory; each warp owns its buffers and
+// its bulk-copy barrier, so the warps of a CTA never wait for each other.
+// ---------------------------------------------------------------------------
+constexpr int kTc3Warps = 2;
+
+template <int N>
+struct TcArgs3 {
+    unsigned m1h[128], m1l[128];   // row-major packed bf16 pairs, as TcArgs2
+    unsigned m2h[128], m2l[128];
+    unsigned m3h[128], m3l[128];
+    const void* X;
+    void* Y;
+    int64_t batch;
+    int beta_zero, alpha_one;
+    float alpha, beta;
+    unsigned* err;
+};
+
+template <int N>
+struct Tc3Layout {
+    static constexpr uint32_t XB = (uint32_t)round_up((size_t)N * N * N * 4, 128);  // FP32 instance
+    static constexpr bool INPLACE = (N == 16);      // T rows overwrite the operand planes
+    static constexpr uint32_t TB = INPLACE ? 0u : 16384u;
+    static constexpr uint32_t PER_WARP = XB + TB;
+};
+
+__device__ __forceinline__ void ldsm_x4_trans(unsigned (&r)[4], uint32_t addr) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr)
+                 : "memory");
+}
+
+// Byte offset of 16-byte chunk c (8 elements) of row p of T, hi half; the lo half
+// follows 512 bytes later.  Rows are 1 KB apart; the chunk index is XOR-ed with
+// the row so that the eight rows read by one ldmatrix matrix, and the eight
+// chunks written by one store instruction, fall in distinct banks.
+__device__ __forceinline__ uint32_t trow_off(int p, int c) {
+    return (uint32_t)(p * 1024 + 16 * ((c ^ (p & 7) ^ ((c >> 3) & 1)) & 31));
+}
+
+template <int N>
+__device__ __forceinline__ float xval(const float* xs, int l, int m, int p) {
+    if constexpr (N == 16) return xs[l + 16 * m + 256 * p];
+    else return (l < N && m < N) ? xs[l + N * m + N * N * p] : 0.f;
+}
+
+// Modes 1 and 2 of plane p: writes row p of T (hi and lo halves).
+template <int N>
+__device__ __forceinline__ void tc3_plane_load(const float* xs, int p, int g, int t, unsigned (&bh)[4],
+                                               unsigned (&bl)[4]) {
+    // B fragment of X_p^T for n-tiles nt = 0, 1: column n = l = 8 nt + g,
+    // rows k = m = 2t, 2t+1 and 2t+8, 2t+9
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) {
+        const int l = 8 * nt + g;
+        split_pair(xval<N>(xs, l, 2 * t, p), xval<N>(xs, l, 2 * t + 1, p), bh[2 * nt], bl[2 * nt]);
+        split_pair(xval<N>(xs, l, 2 * t + 8, p), xval<N>(xs, l, 2 * t + 9, p), bh[2 * nt + 1], bl[2 * nt + 1]);
+    }
+}
+
+__device__ __forceinline__ void tc3_plane_compute(const unsigned (&bh)[4], const unsigned (&bl)[4],
+                                                  const unsigned (&m2h)[4], const unsigned (&m2l)[4],
+                                                  const unsigned (&m1h)[2][2], const unsigned (&m1l)[2][2],
+                                                  float (&z)[2][4]) {
+    float w[2][4];
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) w[nt][e] = 0.f;
+        mma_bf16_16816(w[nt], m2l, bh[2 * nt], bh[2 * nt + 1]);
+        mma_bf16_16816(w[nt], m2h, bl[2 * nt], bl[2 * nt + 1]);
+        mma_bf16_16816(w[nt], m2h, bh[2 * nt], bh[2 * nt + 1]);
+    }
+    unsigned wh[4], wl[4];
+    split_pair(w[0][0], w[0][1], wh[0], wl[0]);
+    split_pair(w[0][2], w[0][3], wh[1], wl[1]);
+    split_pair(w[1][0], w[1][1], wh[2], wl[2]);
+    split_pair(w[1][2], w[1][3], wh[3], wl[3]);
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) z[nt][e] = 0.f;
+        mma_bf16_16816(z[nt], wl, m1h[nt][0], m1h[nt][1]);
+        mma_bf16_16816(z[nt], wh, m1l[nt][0], m1l[nt][1]);
+        mma_bf16_16816(z[nt], wh, m1h[nt][0], m1h[nt][1]);
+    }
+}
+
+// z[nt] = T^T[j' = g, g+8][i = 8 nt + 2t, +1] of plane p -> row p of T, r = i + 16 j'.
+__device__ __forceinline__ void tc3_plane_store(unsigned char* tb, int p, int g, int t, const float (&z)[2][4]) {
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) {
+        unsigned h0, l0, h1, l1;
+        split_pair(z[nt][0], z[nt][1], h0, l0);
+        split_pair(z[nt][2], z[nt][3], h1, l1);
+        const uint32_t o0 = trow_off(p, nt + 2 * g) + 4 * t;
+        const uint32_t o1 = trow_off(p, nt + 2 * g + 16) + 4 * t;
+        *reinterpret_cast<unsigned*>(tb + o0) = h0;
+        *reinterpret_cast<unsigned*>(tb + o0 + 512) = l0;
+        *reinterpret_cast<unsigned*>(tb + o1) = h1;
+        *reinterpret_cast<unsigned*>(tb + o1 + 512) = l1;
+    }
+}
+
+template <int N>
+__device__ __forceinline__ void tc3_rows(const TcArgs3<N>& a, float* yq, uint32_t tb_s, int mt, int lane,
+                                         const unsigned (&m3h)[2][2], const unsigned (&m3l)[2][2]) {
+    const int g = lane >> 2, t = lane & 3, mi = lane >> 3, rr = lane & 7;
+    unsigned ah[4], al[4];
+    const uint32_t to = trow_off(rr + 8 * (mi >> 1), 2 * mt + (mi & 1));
+    ldsm_x4_trans(ah, tb_s + to);
+    ldsm_x4_trans(al, tb_s + to + 512);
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) {
+        float y[4] = {0.f, 0.f, 0.f, 0.f};
+        mma_bf16_16816(y, al, m3h[nt][0], m3h[nt][1]);
+        mma_bf16_16816(y, ah, m3l[nt][0], m3l[nt][1]);
+        mma_bf16_16816(y, ah, m3h[nt][0], m3h[nt][1]);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int i = g + 8 * (e >> 1), k = 8 * nt + 2 * t + (e & 1);
+            if (i < N && k < N) {
+                float* dst = yq + i + N * mt + N * N * k;
+                float v = a.alpha_one ? y[e] : a.alpha * y[e];
+                if (!a.beta_zero) v = fmaf(a.beta, *dst, v);
+                __stcs(dst, v);
+            }
+        }
+    }
+}
+
+template <int N>
+__global__ void __launch_bounds__(32 * kTc3Warps) tc3_kernel(const __grid_constant__ TcArgs3<N> a) {
+    using L = Tc3Layout<N>;
+    constexpr int NX = N * N * N;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, t = lane & 3;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem) + warp;
+    unsigned char* wb = smem + 128 + (size_t)warp * L::PER_WARP;
+    float* xs = reinterpret_cast<float*>(wb);               // FP32 instance (planes of N^2 values)
+    unsigned char* tb = L::INPLACE ? wb : wb + L::XB;        // T rows, 1 KB each
+    const uint32_t tb_s = smem_u32(tb);
+
+    // Constant fragments.  A of M2 (rows j', columns m); B of M1^T and M3^T:
+    // column n of M^T is row n of M, pairs along the row.
+    unsigned m2h[4], m2l[4], m1h[2][2], m1l[2][2], m3h[2][2], m3l[2][2];
+    m2h[0] = a.m2h[g * 8 + t];           m2l[0] = a.m2l[g * 8 + t];
+    m2h[1] = a.m2h[(g + 8) * 8 + t];     m2l[1] = a.m2l[(g + 8) * 8 + t];
+    m2h[2] = a.m2h[g * 8 + t + 4];       m2l[2] = a.m2l[g * 8 + t + 4];
+    m2h[3] = a.m2h[(g + 8) * 8 + t + 4]; m2l[3] = a.m2l[(g + 8) * 8 + t + 4];
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) {
+        const int n = 8 * nt + g;
+        m1h[nt][0] = a.m1h[n * 8 + t];     m1l[nt][0] = a.m1l[n * 8 + t];
+        m1h[nt][1] = a.m1h[n * 8 + t + 4]; m1l[nt][1] = a.m1l[n * 8 + t + 4];
+        m3h[nt][0] = a.m3h[n * 8 + t];     m3l[nt][0] = a.m3l[n * 8 + t];
+        m3h[nt][1] = a.m3h[n * 8 + t + 4]; m3l[nt][1] = a.m3l[n * 8 + t + 4];
+    }
+    if constexpr (!L::INPLACE) {
+        // rows p >= N of T stay zero for the whole kernel
+        for (int e = lane; e < (16 - N) * 256; e += 32)
+            reinterpret_cast<unsigned*>(tb + N * 1024)[e] = 0u;
+    }
+
+    const int64_t nwarps = (int64_t)gridDim.x * kTc3Warps;
+    int64_t inst = (int64_t)blockIdx.x * kTc3Warps + warp;
+    uint64_t pol = 0;
+    if (lane == 0) {
+        mbar_init(bar, 1);
+        fence_barrier_init();
+        pol = l2_evict_first_policy();
+        if (inst < a.batch) {
+            mbar_arrive_expect_tx(bar, NX * 4);
+            bulk_g2s(xs, static_cast<const float*>(a.X) + inst * NX, NX * 4, bar, pol);
+        }
+    }
+    __syncwarp();
+    unsigned phase = 0;
+    for (; inst < a.batch; inst += nwarps, phase ^= 1u) {
+        if (!mbar_wait_bounded(bar, phase, a.err)) return;   // nothing else in flight
+
+        // ---- modes 1 and 2, two planes per step ------------------------------------------
+#pragma unroll 1
+        for (int p = 0; p < N; p += 2) {
+            const bool two = p + 1 < N;
+            unsigned bh0[4], bl0[4], bh1[4], bl1[4];
+            tc3_plane_load<N>(xs, p, g, t, bh0, bl0);
+            if (two) tc3_plane_load<N>(xs, p + 1, g, t, bh1, bl1);
+            float z0[2][4], z1[2][4];
+            tc3_plane_compute(bh0, bl0, m2h, m2l, m1h, m1l, z0);
+            if (two) tc3_plane_compute(bh1, bl1, m2h, m2l, m1h, m1l, z1);
+            __syncwarp();   // planes p, p+1 are read by every lane before they are overwritten
+            tc3_plane_store(tb, p, g, t, z0);
+            if (two) tc3_plane_store(tb, p + 1, g, t, z1);
+        }
+        __syncwarp();
+
+        // ---- mode 3, two row blocks per step ---------------------------------------------
+        float* yq = static_cast<float*>(a.Y) + inst * NX;
+#pragma unroll 1
+        for (int mt = 0; mt < N; mt += 2) {
+            tc3_rows<N>(a, yq, tb_s, mt, lane, m3h, m3l);
+            if (mt + 1 < N) tc3_rows<N>(a, yq, tb_s, mt + 1, lane, m3h, m3l);
+        }
+        __syncwarp();   // T and the operand planes are free: fetch the next instance
+        if (lane == 0) {
+            const int64_t next = inst + nwarps;
+            if (next < a.batch) {
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(bar, NX * 4);
+                bulk_g2s(xs, static_cast<const float*>(a.X) + next * NX, NX * 4, bar, pol);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
 // float -> bfloat16 bits, round to nearest even (NaN kept quiet).
@@ -314,6 +546,57 @@ static kron_status launch_tc2_n(const KronDesc& d, cudaStream_t st) {
     return cudaPeekAtLastError() == cudaSuccess ? KRON_OK : KRON_ERR_CUDA;
 }
 
+template <int N>
+static kron_status launch_tc3_n(const KronDesc& d, cudaStream_t st) {
+    const DeviceInfo& dev = device_info();
+    if (dev.sms <= 0) return KRON_ERR_CUDA;
+    TcArgs3<N> a;
+    split_rowmajor(d.m1, N, a.m1h, a.m1l);
+    split_rowmajor(d.m2, N, a.m2h, a.m2l);
+    split_rowmajor(d.m3, N, a.m3h, a.m3l);
+    a.X = d.X;
+    a.Y = d.Y;
+    a.batch = d.batch;
+    a.alpha = (float)d.alpha;
+    a.beta = (float)d.beta;
+    a.beta_zero = d.beta == 0.0;
+    a.alpha_one = d.alpha == 1.0;
+    a.err = device_error_word();
+    if (!a.err) return KRON_ERR_CUDA;
+    const size_t smem = 128 + kTc3Warps * (size_t)Tc3Layout<N>::PER_WARP;
+    if (smem > dev.smem_per_block_optin) return KRON_ERR_NOT_SUPPORTED;
+    auto kern = tc3_kernel<N>;
+    static int smem_set = 0;
+    if ((int)smem > smem_set) {
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return KRON_ERR_CUDA;
+        smem_set = (int)smem;
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * kTc3Warps, smem) != cudaSuccess)
+        return KRON_ERR_CUDA;
+    int64_t grid = d.grid > 0 ? d.grid : (int64_t)(per_sm < 1 ? 1 : per_sm) * dev.sms;
+    const int64_t need = (d.batch + kTc3Warps - 1) / kTc3Warps;
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    kern<<<(unsigned)grid, 32 * kTc3Warps, smem, st>>>(a);
+    return cudaPeekAtLastError() == cudaSuccess ? KRON_OK : KRON_ERR_CUDA;
+}
+
+static kron_status launch_tc3(const KronDesc& d, cudaStream_t st) {
+    switch (d.N) {   // even sizes: an FP32 instance is a whole number of 16-byte units
+        case 2: return launch_tc3_n<2>(d, st);
+        case 4: return launch_tc3_n<4>(d, st);
+        case 6: return launch_tc3_n<6>(d, st);
+        case 8: return launch_tc3_n<8>(d, st);
+        case 10: return launch_tc3_n<10>(d, st);
+        case 12: return launch_tc3_n<12>(d, st);
+        case 14: return launch_tc3_n<14>(d, st);
+        case 16: return launch_tc3_n<16>(d, st);
+        default: return KRON_ERR_NOT_SUPPORTED;
+    }
+}
+
 template <typename S>
 static kron_status launch_tc2(const KronDesc& d, cudaStream_t st) {
     switch (d.N) {
@@ -348,6 +631,7 @@ kron_status launch_tc(const KronDesc& d, cudaStream_t st) {
         if (d.io == KRON_R16BF) return launch_tc2<__nv_bfloat16>(d, st);
         return KRON_ERR_NOT_SUPPORTED;
     }
+    if (d.io == KRON_R32F) return launch_tc3(d, st);
     return KRON_ERR_NOT_SUPPORTED;
 }
 

@@ -92,3 +92,47 @@ def test_bf16x3_rejects_unsupported_layouts():
         kg.kron2_batched(np.eye(8), np.eye(8), Xd, torch.zeros_like(Xd), ma=8, na=8, mb=8, nb=8, batch=8,
                          compute="bf16x3")
     assert e.value.status == 2
+
+
+@pytest.mark.parametrize("n", [2, 4, 6, 8, 10, 12, 14, 16])
+def test_bf16x3_3d_even_sizes(n):
+    b = inputs.make_batch(3, n, 203, seed=400 + n, x_dist="normal")
+    Y, X64 = run_gpu(b, io="f32", compute="bf16x3", guard=16)
+    err = max_norm_err(Y, oracle_ref(b, X64), b, X64)
+    assert err <= bound(3, n)
+    assert err <= 1e-5, err
+
+
+def test_bf16x3_3d_alpha_beta():
+    n = 16
+    b = inputs.make_batch(3, n, 37, seed=410, x_dist="normal")
+    Y0 = np.random.default_rng(2).standard_normal(b.batch * n ** 3).astype(np.float32).astype(np.float64)
+    Y, X64 = run_gpu(b, io="f32", compute="bf16x3", alpha=-0.5, beta=1.5, Y0=Y0, guard=8)
+    ref = oracle_ref(b, X64, alpha=-0.5, beta=1.5, Y=Y0)
+    assert max_norm_err(Y, ref, b, X64) <= 2 * bound(3, n) + 1e-6
+
+
+def test_bf16x3_3d_full_size_sampled():
+    import torch
+    batch, n = 1 << 16, 16
+    b = inputs.make_batch(3, n, batch, seed=5, x_dist="normal")
+    X = torch.from_numpy(b.X).cuda()
+    Y = torch.empty_like(X)
+    kg.kron3_batched(b.A, b.B, b.C, X, Y, ma=n, na=n, mb=n, nb=n, mc=n, nc=n, batch=batch, compute="bf16x3")
+    torch.cuda.synchronize()
+    assert kg.device_status() == 0
+    idx = np.sort(np.random.default_rng(7).choice(batch, 256, replace=False))
+    idx[-1] = batch - 1
+    Xs = b.X.reshape(batch, 4096)[idx].astype(np.float64).ravel()
+    sub = inputs.Batch(3, n, len(idx), b.A, b.B, b.C, Xs)
+    got = Y.view(batch, 4096)[torch.from_numpy(idx).cuda()].double().cpu().numpy().ravel()
+    assert max_norm_err(got, oracle_ref(sub, Xs), sub, Xs) <= 1e-5
+
+
+def test_bf16x3_3d_odd_size_not_supported():
+    import torch
+    X = torch.zeros(5 * 125, device="cuda")
+    with pytest.raises(kg.KronError) as e:
+        kg.kron3_batched(np.eye(5), np.eye(5), np.eye(5), X, torch.zeros_like(X), ma=5, na=5, mb=5, nb=5, mc=5,
+                         nc=5, batch=5, compute="bf16x3")
+    assert e.value.status == 2
