@@ -199,3 +199,73 @@ def autotune(kind, n, batch, X, Y, compute="native", stream=None):
                                         _io_of(X), COMPUTE[compute], ctypes.byref(p), ctypes.byref(d)),
            "kron_autotune")
     return p.value, d.value
+
+
+class _ClassDesc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("n", ctypes.c_int), ("A", ctypes.c_void_p), ("B", ctypes.c_void_p),
+                ("C", ctypes.c_void_p)]
+
+
+class VarlenPlan:
+    """Mixed-size batch plan (kron_varlen_plan_*): one persistent, graph-captured launch.
+
+    classes: list of (kind, n, A, B[, C]) with n x n host components (2-D arrays are
+    taken as matrices, 1-D as column-major); class_of[p], x_off[p], y_off[p] give each
+    instance's class and element offsets into X and Y.
+    """
+
+    def __init__(self, classes, class_of, x_off, y_off, io="f32", compute="native"):
+        L = load_library()
+        self._keep = []
+        descs = (_ClassDesc * max(1, len(classes)))()
+        for i, c in enumerate(classes):
+            kind, n = int(c[0]), int(c[1])
+            mats = []
+            for M in c[2:2 + kind]:
+                buf, _ = _comp_buffer(M, np.float32)
+                self._keep.append(buf)
+                mats.append(buf.ctypes.data)
+            A, B = mats[0], mats[1]
+            C = mats[2] if kind == 3 else None
+            descs[i] = _ClassDesc(kind, n, A, B, C)
+        self._cls = np.ascontiguousarray(class_of, dtype=np.int32)
+        self._xo = np.ascontiguousarray(x_off, dtype=np.int64)
+        self._yo = np.ascontiguousarray(y_off, dtype=np.int64)
+        self.batch = len(self._cls)
+        h = ctypes.c_void_p()
+        _check(L.kron_varlen_plan_create(ctypes.byref(h), len(classes), ctypes.addressof(descs), self.batch,
+                                         self._cls.ctypes.data, self._xo.ctypes.data, self._yo.ctypes.data,
+                                         DTYPES[io], COMPUTE[compute]), "kron_varlen_plan_create")
+        self.handle = h
+        self.io = io
+
+    def workspace_size(self) -> int:
+        s = ctypes.c_size_t()
+        _check(load_library().kron_varlen_workspace_size(self.handle, ctypes.byref(s)),
+               "kron_varlen_workspace_size")
+        return s.value
+
+    def alloc_workspace(self, device=None):
+        torch = _torch()
+        return torch.empty(max(1, self.workspace_size()), dtype=torch.uint8, device=device or "cuda")
+
+    def execute(self, X, Y, workspace, stream=None):
+        _check(load_library().kron_varlen_execute(self.handle, X.data_ptr(), Y.data_ptr(), workspace.data_ptr(),
+                                                  workspace.numel(), _stream_handle(stream)),
+               "kron_varlen_execute")
+        return Y
+
+    def tune(self, X, Y, workspace, stream=None):
+        _check(load_library().kron_varlen_tune(self.handle, X.data_ptr(), Y.data_ptr(), workspace.data_ptr(),
+                                               workspace.numel(), _stream_handle(stream)), "kron_varlen_tune")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load_library().kron_varlen_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

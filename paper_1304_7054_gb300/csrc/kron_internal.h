@@ -45,6 +45,10 @@ size_t elem_size(kron_dtype t);
 
 // Fills d.P / d.nstage from the tile-configuration table, if it has an entry.
 void apply_tile_config(KronDesc& d);
+// Appends one entry to the tuning cache file (KRON_TUNE_CACHE), if set.
+void tune_cache_append(int kind, int n, kron_dtype io, kron_compute comp, int P, int nstage);
+// Compute-mode key under which the mixed-size path stores its per-class tile sizes.
+constexpr int kVarlenTag = 7;
 
 // Device status word of the current device (device pointer).
 unsigned* device_error_word();

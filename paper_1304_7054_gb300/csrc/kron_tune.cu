@@ -76,6 +76,11 @@ void apply_tile_config(KronDesc& d) {
     }
 }
 
+void tune_cache_append(int kind, int n, kron_dtype io, kron_compute comp, int P, int nstage) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    append_cache(Key(kind, n, (int)io, (int)comp), Entry{P, nstage});
+}
+
 }  // namespace kron
 
 using namespace kron;

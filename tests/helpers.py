@@ -10,6 +10,10 @@ TOL = {"f32": 1e-5, "f64": 1e-13,
        # output rounding to the 16-bit storage type: half an ulp relative to |y|,
        # |y| <= ||A|| ||B|| ||X|| (Cauchy-Schwarz), plus the FP32 accumulation error
        "bf16": 2.0 ** -8 + 1e-5, "f16": 2.0 ** -11 + 1e-5}
+# Below the smallest normal float16 (2^-14) rounding is absolute: half the
+# subnormal spacing, 2^-25.  It is subtracted from each difference before the
+# normalisation (bfloat16 shares FP32's exponent range, so it has no such floor).
+ABS_FLOOR = {"f16": 2.0 ** -25}
 
 
 def torch_dtype(io):
@@ -49,9 +53,9 @@ def oracle_ref(b, X64, **kw):
     return oracle.kron3(b.A, b.B, b.C, X64, ma=n, na=n, mb=n, nb=n, mc=n, nc=n, batch=b.batch, **kw)
 
 
-def max_norm_err(Y, Yref, b, X64):
+def max_norm_err(Y, Yref, b, X64, io=None):
     inst = b.n ** b.kind
     Y = np.asarray(Y, dtype=np.float64)[: b.batch * inst].reshape(b.batch, inst)
     R = np.asarray(Yref, dtype=np.float64)[: b.batch * inst].reshape(b.batch, inst)
-    d = np.abs(Y - R).max(axis=1)
+    d = np.maximum(np.abs(Y - R) - ABS_FLOOR.get(io, 0.0), 0.0).max(axis=1)
     return float((d / (comp_norm(b) * x_norms(X64, b.batch, inst))).max())

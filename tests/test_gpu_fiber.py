@@ -87,7 +87,7 @@ def test_16bit_storage(kind, n, io):
     b = inputs.make_batch(kind, n, batch, seed=200 + n + kind, x_dist="normal")
     Y, X64 = run_gpu(b, io=io, guard=16)
     ref = oracle_ref(b, X64)   # oracle on the stored (rounded) operand values
-    assert max_norm_err(Y, ref, b, X64) <= TOL[io]
+    assert max_norm_err(Y, ref, b, X64, io) <= TOL[io]
 
 
 # --- exact cases ------------------------------------------------------------------------------

@@ -1,0 +1,166 @@
+"""Parity of the mixed-size persistent path (one graph-captured launch) with the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1304_7054_gb300 as kg
+from paper_1304_7054_gb300 import inputs
+
+from helpers import ABS_FLOOR, TOL, torch_dtype
+
+pytestmark = pytest.mark.gpu
+
+
+def classes_of(v):
+    return [(k, n, *cs) for (k, n), cs in zip(v.classes, v.comps)]
+
+
+def reference(v, X64, idx=None):
+    """Oracle output per instance (dict p -> flat array) and the normalising factor."""
+    idx = np.arange(len(v.class_of)) if idx is None else idx
+    out, norm = {}, {}
+    for c, (kind, n) in enumerate(v.classes):
+        sel = idx[v.class_of[idx] == c]
+        if len(sel) == 0:
+            continue
+        nx = n ** kind
+        Xs = np.concatenate([X64[v.x_off[p]:v.x_off[p] + nx] for p in sel])
+        cs = v.comps[c]
+        if kind == 2:
+            Y = oracle.kron2(cs[0], cs[1], Xs, ma=n, na=n, mb=n, nb=n, batch=len(sel))
+        else:
+            Y = oracle.kron3(cs[0], cs[1], cs[2], Xs, ma=n, na=n, mb=n, nb=n, mc=n, nc=n, batch=len(sel))
+        cn = np.prod([np.linalg.norm(np.asarray(M, np.float64)) for M in cs])
+        for r, p in enumerate(sel):
+            out[p] = Y[r * nx:(r + 1) * nx]
+            norm[p] = cn * np.linalg.norm(Xs[r * nx:(r + 1) * nx])
+    return out, norm
+
+
+def max_err(v, Y, ref, norm, io="f32"):
+    e = 0.0
+    for p, r in ref.items():
+        n = v.classes[v.class_of[p]][1] ** v.classes[v.class_of[p]][0]
+        d = np.maximum(np.abs(Y[v.y_off[p]:v.y_off[p] + n] - r) - ABS_FLOOR.get(io, 0.0), 0.0)
+        e = max(e, d.max() / max(norm[p], 1e-300))
+    return e
+
+
+def run(v, io="f32", plan=None, Y=None, ws=None):
+    import torch
+    if io == "f32":
+        X = torch.from_numpy(v.X).cuda()
+        X64 = v.X.astype(np.float64)
+    else:
+        t = inputs.to_storage(v.X, io)
+        X, X64 = t.cuda(), inputs.storage_to_f64(t)
+    plan = plan or kg.VarlenPlan(classes_of(v), v.class_of, v.x_off, v.y_off, io=io)
+    Y = Y if Y is not None else torch.full((v.total,), float("nan"), dtype=torch_dtype(io), device="cuda")
+    ws = ws if ws is not None else plan.alloc_workspace()
+    plan.execute(X, Y, ws)
+    torch.cuda.synchronize()
+    assert kg.device_status() == 0
+    return plan, X, Y, ws, X64
+
+
+@pytest.mark.parametrize("io", ["f32", "bf16", "f16"])
+def test_varlen_all_classes(io):
+    v = inputs.make_varlen(3000, seed=11, nmin=1, nmax=16)
+    plan, X, Y, ws, X64 = run(v, io)
+    ref, norm = reference(v, X64)
+    Yh = Y.double().cpu().numpy()
+    assert not np.isnan(Yh).any()
+    err = max_err(v, Yh, ref, norm, io)
+    assert err <= TOL[io], err
+    plan.close()
+
+
+def test_varlen_graph_replay_is_deterministic_and_pointers_update():
+    import torch
+    v = inputs.make_varlen(2000, seed=12)
+    plan, X, Y, ws, X64 = run(v)
+    Y1 = Y.clone()
+    plan.execute(X, Y, ws)
+    torch.cuda.synchronize()
+    assert torch.equal(Y, Y1)
+    Y2 = torch.zeros_like(Y)   # another output buffer: the graph's kernel node is updated
+    plan.execute(X, Y2, ws)
+    torch.cuda.synchronize()
+    assert torch.equal(Y2, Y1)
+    plan.close()
+
+
+def test_varlen_matches_per_size_launches():
+    import torch
+    v = inputs.make_varlen(2500, seed=13)
+    plan, X, Y, ws, X64 = run(v)
+    Yh = Y.double().cpu().numpy()
+    for c, (kind, n) in enumerate(v.classes):
+        sel = np.nonzero(v.class_of == c)[0]
+        if len(sel) == 0:
+            continue
+        nx = n ** kind
+        Xs = torch.from_numpy(np.concatenate([v.X[v.x_off[p]:v.x_off[p] + nx] for p in sel])).cuda()
+        Ys = torch.empty_like(Xs)
+        cs = v.comps[c]
+        if kind == 2:
+            kg.kron2_batched(cs[0], cs[1], Xs, Ys, ma=n, na=n, mb=n, nb=n, batch=len(sel))
+        else:
+            kg.kron3_batched(cs[0], cs[1], cs[2], Xs, Ys, ma=n, na=n, mb=n, nb=n, mc=n, nc=n, batch=len(sel))
+        got = np.concatenate([Yh[v.y_off[p]:v.y_off[p] + nx] for p in sel])
+        exp = Ys.double().cpu().numpy()
+        assert np.abs(got - exp).max() <= 1e-5 * max(1.0, np.abs(exp).max()) * n
+    plan.close()
+
+
+def test_varlen_single_instance_class_and_missing_classes():
+    import torch
+    rng = np.random.default_rng(3)
+    A2, B2 = rng.uniform(-1, 1, (5, 5)), rng.uniform(-1, 1, (5, 5))
+    A3, B3, C3 = (rng.uniform(-1, 1, (3, 3)) for _ in range(3))
+    classes = [(2, 5, A2, B2), (3, 3, A3, B3, C3), (2, 16, np.eye(16), np.eye(16))]   # class 2 unused
+    class_of = [1, 0, 0, 0]
+    sizes = [27, 25, 25, 25]
+    x_off = np.concatenate([[0], np.cumsum(sizes)[:-1]])
+    total = int(sum(sizes))
+    X = rng.standard_normal(total).astype(np.float32)
+    plan = kg.VarlenPlan(classes, class_of, x_off, x_off)
+    ws = plan.alloc_workspace()
+    Y = torch.full((total,), float("nan"), device="cuda")
+    plan.execute(torch.from_numpy(X).cuda(), Y, ws)
+    torch.cuda.synchronize()
+    Yh = Y.double().cpu().numpy()
+    col = lambda M: np.ascontiguousarray(np.asarray(M).T).ravel()
+    r3 = oracle.kron3(col(A3), col(B3), col(C3), X[:27].astype(np.float64), ma=3, na=3, mb=3, nb=3, mc=3, nc=3,
+                      batch=1)
+    np.testing.assert_allclose(Yh[:27], r3, atol=1e-5)
+    r2 = oracle.kron2(col(A2), col(B2), X[27:].astype(np.float64), ma=5, na=5, mb=5, nb=5, batch=3)
+    np.testing.assert_allclose(Yh[27:], r2, atol=1e-5)
+    plan.close()
+
+
+def test_varlen_tune_keeps_results():
+    import torch
+    v = inputs.make_varlen(4000, seed=14)
+    plan, X, Y, ws, X64 = run(v)
+    Y1 = Y.clone()
+    plan.tune(X, Y, ws)
+    Y.fill_(float("nan"))
+    plan.execute(X, Y, ws)
+    torch.cuda.synchronize()
+    ref, norm = reference(v, X64)
+    assert max_err(v, Y.double().cpu().numpy(), ref, norm) <= TOL["f32"]
+    plan.close()
+
+
+@pytest.mark.parametrize("io", ["f32", "bf16"])
+def test_varlen_full_size_sampled(io):
+    """The mixed-size workload the benchmark times: 200,000 instances, n ~ U{4..16}."""
+    v = inputs.make_varlen(200000, seed=5)
+    plan, X, Y, ws, X64 = run(v, io)
+    rng = np.random.default_rng(8)
+    idx = np.sort(rng.choice(200000, 3000, replace=False))
+    idx[-1] = 199999
+    ref, norm = reference(v, X64, idx)
+    assert max_err(v, Y.double().cpu().numpy(), ref, norm, io) <= TOL[io]
+    plan.close()
