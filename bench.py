@@ -49,6 +49,15 @@ WORKLOADS = {
     "kron2-bf16x3-n16": dict(kind=2, n=16, batch=1 << 20, io="f32", compute="bf16x3", seed=4),
     "kron3-bf16x3-n16": dict(kind=3, n=16, batch=1 << 16, io="f32", compute="bf16x3", seed=4),
     "kron2-bf16-bf16x3-n16": dict(kind=2, n=16, batch=1 << 20, io="bf16", compute="bf16x3", seed=4),
+    "kron2-bf16-n8": dict(kind=2, n=8, batch=1 << 20, io="bf16", compute="native", seed=4),
+    "kron2-bf16-n12": dict(kind=2, n=12, batch=1 << 20, io="bf16", compute="native", seed=4),
+    "kron2-f16-n12": dict(kind=2, n=12, batch=1 << 20, io="f16", compute="native", seed=4),
+    "kron2-bf16x3-n8": dict(kind=2, n=8, batch=1 << 20, io="f32", compute="bf16x3", seed=4),
+    "kron2-bf16x3-n12": dict(kind=2, n=12, batch=1 << 20, io="f32", compute="bf16x3", seed=4),
+    "kron3-bf16x3-n10": dict(kind=3, n=10, batch=1 << 18, io="f32", compute="bf16x3", seed=4),
+    "kron3-bf16-n16": dict(kind=3, n=16, batch=1 << 16, io="bf16", compute="native", seed=4),
+    "kron3-f64-n10": dict(kind=3, n=10, batch=1 << 18, io="f64", compute="native", seed=2),
+    "kron2-f64-n10": dict(kind=2, n=10, batch=1 << 20, io="f64", compute="native", seed=1),
 }
 HEADLINE = "kron2-f32-n16"
 ESIZE = {"f32": 4, "f64": 8, "bf16": 2, "f16": 2}
@@ -285,10 +294,102 @@ def measure_variant(kg, name, steps, warmup, torch, dev, peaks):
     gbs = by / (kern_ms * 1e-3) / 1e9
     r = {"gflops": round(fl / (kern_ms * 1e-3) / 1e9, 1), "hbm_gbs": round(gbs, 1),
          "hbm_frac": round(gbs / peaks["hbm"], 4), "ms": round(kern_ms, 4), "batch": b.batch,
-         "max_norm_err_vs_fp64_oracle": err}
+         "kernel": kernel_of(b.kind, b.n, wl["io"], wl["compute"]), "max_norm_err_vs_fp64_oracle": err}
     del X, Y
     torch.cuda.empty_cache()
     return r
+
+
+def kernel_of(kind, n, io, compute):
+    """Name of the kernel the library dispatches a contiguous batch to."""
+    if compute == "bf16x3":
+        return f"tc{kind}_kernel<n={n},{io}>"
+    if io != "f64" and n % 2 == 0:
+        return f"pair_kernel<{io},n={n},{kind}-D>"
+    return f"fiber_kernel<{io},n={n},{kind}-D>"
+
+
+def varlen_stats(v, io):
+    fl = sum(4 * n ** 3 if k == 2 else 6 * n ** 4 for k, n in (v.classes[c] for c in v.class_of))
+    by = 2 * ESIZE[io] * v.total
+    return fl, by
+
+
+def measure_varlen(kg, io, steps, warmup, torch, dev, peaks, count=200000, seed=5):
+    """Mixed-size batch (n ~ U{4..16}, 2-D/3-D 50/50): one graph launch, tuned tiles;
+    next to it, the same instances as 26 per-size plain launches (one per class)."""
+    from paper_1304_7054_gb300 import inputs
+    v = inputs.make_varlen(count, seed=seed)
+    X = (torch.from_numpy(v.X) if io == "f32" else inputs.to_storage(v.X, io)).to(dev)
+    Y = torch.empty_like(X)
+    classes = [(k, n, *cs) for (k, n), cs in zip(v.classes, v.comps)]
+    plan = kg.VarlenPlan(classes, v.class_of, v.x_off, v.y_off, io=io)
+    ws = plan.alloc_workspace(dev)
+    plan.execute(X, Y, ws)
+    plan.tune(X, Y, ws)
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        plan.execute(X, Y, ws)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        plan.execute(X, Y, ws)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    fl, by = varlen_stats(v, io)
+    # error on a seeded sample against the FP64 oracle
+    import oracle
+    rng = np.random.default_rng(8)
+    idx = np.sort(rng.choice(count, 512, replace=False))
+    Yh = Y.double().cpu().numpy()
+    Xh = X.double().cpu().numpy()
+    err = 0.0
+    for p in idx:
+        k, n = v.classes[v.class_of[p]]
+        cs = v.comps[v.class_of[p]]
+        nx = n ** k
+        xp = Xh[v.x_off[p]:v.x_off[p] + nx]
+        if k == 2:
+            r = oracle.kron2(cs[0], cs[1], xp, ma=n, na=n, mb=n, nb=n, batch=1)
+        else:
+            r = oracle.kron3(cs[0], cs[1], cs[2], xp, ma=n, na=n, mb=n, nb=n, mc=n, nc=n, batch=1)
+        nrm = np.prod([np.linalg.norm(np.asarray(M, np.float64)) for M in cs]) * np.linalg.norm(xp)
+        err = max(err, float(np.abs(Yh[v.y_off[p]:v.y_off[p] + nx] - r).max() / nrm))
+    # per-size plain launches on class-contiguous copies of the same instances
+    groups = []
+    for c, (k, n) in enumerate(v.classes):
+        sel = np.nonzero(v.class_of == c)[0]
+        if len(sel):
+            nx = n ** k
+            gx = np.concatenate([v.X[v.x_off[p]:v.x_off[p] + nx] for p in sel])
+            gX = (torch.from_numpy(gx) if io == "f32" else inputs.to_storage(gx, io)).to(dev)
+            groups.append((k, n, v.comps[c], gX, torch.empty_like(gX), len(sel)))
+
+    def per_size():
+        for k, n, cs, gX, gY, cnt in groups:
+            if k == 2:
+                kg.kron2_batched(cs[0], cs[1], gX, gY, ma=n, na=n, mb=n, nb=n, batch=cnt)
+            else:
+                kg.kron3_batched(cs[0], cs[1], cs[2], gX, gY, ma=n, na=n, mb=n, nb=n, mc=n, nc=n, batch=cnt)
+
+    for _ in range(warmup):
+        per_size()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        per_size()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_ps = e0.elapsed_time(e1) / steps
+    plan.close()
+    gbs = by / (ms * 1e-3) / 1e9
+    return {"gflops": round(fl / (ms * 1e-3) / 1e9, 1), "hbm_gbs": round(gbs, 1),
+            "hbm_frac": round(gbs / peaks["hbm"], 4), "ms": round(ms, 4), "instances": count,
+            "launches_per_step": 1, "max_norm_err_vs_fp64_oracle": err,
+            "per_size_plain_launches": {"launches_per_step": len(groups), "ms": round(ms_ps, 4),
+                                        "gflops": round(fl / (ms_ps * 1e-3) / 1e9, 1)}}
 
 
 def traffic_for(kernel_name):
@@ -340,7 +441,7 @@ def run_ours(args):
     fl = flops_per_instance(b.kind, b.n) * b.batch
     by = 2 * ESIZE[wl["io"]] * b.n ** b.kind * b.batch
     value = world * fl / (ms * 1e-3) / 1e9
-    kernel_name = f"fiber_kernel<{wl['io']},{b.n},{b.kind}>"
+    kernel_name = kernel_of(b.kind, b.n, wl["io"], wl["compute"])
     achieved = by / (kern_ms * 1e-3) / 1e9
     del X, Y
     torch.cuda.empty_cache()
@@ -352,6 +453,9 @@ def run_ours(args):
             for name in WORKLOADS:
                 if name != args.workload:
                     variants[name] = measure_variant(kg, name, max(5, min(args.steps, 30)), 3, torch, dev, peaks)
+            for io in ("f32", "bf16"):
+                variants[f"varlen-{io}"] = measure_varlen(kg, io, max(5, min(args.steps, 30)), 3, torch, dev,
+                                                          peaks)
         cpu = cpu_baseline(b, seconds=args.cpu_seconds)
         out = {
             "metric": METRIC, "value": round(value, 1), "unit": "GFlop/s", "n_gpus": world,

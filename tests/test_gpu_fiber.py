@@ -2,7 +2,7 @@
 
 Every call goes through the C ABI (ctypes binding).  Floating-point parity is
 checked per instance against the FP64 oracle with the normalised error of the
-north-star (max |Y - Y_ref| / (||A|| ||B|| (||C||) ||X^p||)): FP32 <= 1e-5,
+target accuracy (max |Y - Y_ref| / (||A|| ||B|| (||C||) ||X^p||)): FP32 <= 1e-5,
 FP64 <= 1e-13, 16-bit storage within half an ulp of the output type.  Exact
 cases (identity, permutations, powers of two) are compared bit for bit.
 """
