@@ -211,6 +211,36 @@ KRON_API kron_status kron_varlen_tune(kron_varlen_plan* plan, const void* X, voi
                                       kron_stream_t stream);
 KRON_API kron_status kron_varlen_plan_destroy(kron_varlen_plan* plan);
 
+/*
+ * kron_varlen_execute_noalloc -- the paper has no counterpart; this entry point
+ * is for callers that cannot allocate device memory.  Examples: code that runs
+ * while another component owns every byte of device memory through its own
+ * allocator and hands out no scratch buffer, and latency-critical loops where
+ * cudaMalloc / cudaFree would synchronise the device.  It computes the same
+ * result as kron_varlen_execute on the same plan, X and Y, but takes no
+ * workspace.  The plan's tables go into one fixed 8 MiB device array inside the
+ * library.  Every GPU that loads the library holds that array until the process
+ * exits.
+ *
+ *  - Limit: the plan needs 32 bytes of tables per instance, so at most 262,144
+ *    instances.  Larger plans are rejected with KRON_ERR_WORKSPACE before any
+ *    device work.
+ *  - It calls no cudaMalloc, cudaFree or other allocating routine, and launches
+ *    the kernel directly (no graph).
+ *  - The first call on a device looks up the array's device address with that
+ *    device current.  Make that first call before any stream capture.
+ *  - Every call copies its tables into the array (a host-to-device copy from
+ *    pageable memory; the call waits for it) and then launches.  Nothing is
+ *    kept between calls.  All calls on a device share the one array, so calls
+ *    whose work overlaps on the GPU (other streams, other host threads) race;
+ *    serialise them.
+ *  - Errors: as kron_varlen_execute (KRON_ERR_INVALID_VALUE, KRON_ERR_ALIAS,
+ *    KRON_ERR_NOT_SUPPORTED, KRON_ERR_CUDA), plus KRON_ERR_WORKSPACE for a batch
+ *    above the limit.
+ */
+KRON_API kron_status kron_varlen_execute_noalloc(kron_varlen_plan* plan, const void* X, void* Y,
+                                                 kron_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -45,6 +45,7 @@ SIGNATURES = {
     "kron_varlen_execute": ([_P, _P, _P, _P, _S, _P], _I),
     "kron_varlen_tune": ([_P, _P, _P, _P, _S, _P], _I),
     "kron_varlen_plan_destroy": ([_P], _I),
+    "kron_varlen_execute_noalloc": ([_P, _P, _P, _P], _I),
 }
 
 _lib = None
@@ -253,6 +254,13 @@ class VarlenPlan:
         _check(load_library().kron_varlen_execute(self.handle, X.data_ptr(), Y.data_ptr(), workspace.data_ptr(),
                                                   workspace.numel(), _stream_handle(stream)),
                "kron_varlen_execute")
+        return Y
+
+    def execute_noalloc(self, X, Y, stream=None):
+        """Same result as execute(), with the library's fixed device array as the
+        workspace (no allocation anywhere; at most 262,144 instances)."""
+        _check(load_library().kron_varlen_execute_noalloc(self.handle, X.data_ptr(), Y.data_ptr(),
+                                                          _stream_handle(stream)), "kron_varlen_execute_noalloc")
         return Y
 
     def tune(self, X, Y, workspace, stream=None):

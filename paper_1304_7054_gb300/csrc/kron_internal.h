@@ -49,6 +49,9 @@ void apply_tile_config(KronDesc& d);
 void tune_cache_append(int kind, int n, kron_dtype io, kron_compute comp, int P, int nstage);
 // Compute-mode key under which the mixed-size path stores its per-class tile sizes.
 constexpr int kVarlenTag = 7;
+// Size of the fixed device array used by kron_varlen_execute_noalloc (32 bytes
+// of tables per instance: up to 262,144 instances).
+constexpr size_t kVarlenNoallocScratchBytes = (size_t)8 << 20;
 
 // Device status word of the current device (device pointer).
 unsigned* device_error_word();

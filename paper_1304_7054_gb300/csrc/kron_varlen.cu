@@ -626,6 +626,66 @@ KRON_API kron_status kron_varlen_tune(kron_varlen_plan* plan, const void* X, voi
     return st;
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free execute.  The tables go into a fixed file-scope device array
+// instead of a caller workspace.  Its device address is looked up once per
+// device (with that device current) by the first call on that device.  Every
+// call rewrites the tables it needs before its launch, so no state is carried
+// over; concurrent calls on the same device share the array and would race.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_varlen_noalloc_scratch[kron::kVarlenNoallocScratchBytes];
+
+static void* noalloc_scratch() {
+    static void* ptr[64] = {};
+    static std::mutex mu;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_varlen_noalloc_scratch) != cudaSuccess) return nullptr;
+        ptr[dev] = p;
+    }
+    return ptr[dev];
+}
+
+KRON_API kron_status kron_varlen_execute_noalloc(kron_varlen_plan* plan, const void* X, void* Y,
+                                                 kron_stream_t stream) {
+    if (!plan) return KRON_ERR_INVALID_VALUE;
+    if (plan->batch == 0) return KRON_OK;
+    if (plan->ws_bytes > kVarlenNoallocScratchBytes) return KRON_ERR_WORKSPACE;   // batch above the maximum
+    if (!X || !Y) return KRON_ERR_INVALID_VALUE;
+    const size_t es = elem_size(plan->io);
+    if (((uintptr_t)X) % es || ((uintptr_t)Y) % es) return KRON_ERR_INVALID_VALUE;
+    const uintptr_t x0 = (uintptr_t)X, x1 = x0 + plan->x_total * es;
+    const uintptr_t y0 = (uintptr_t)Y, y1 = y0 + plan->y_total * es;
+    if (x0 < y1 && y0 < x1) return KRON_ERR_ALIAS;
+    if (plan->tiles.empty()) return KRON_OK;
+    const DeviceInfo& dev = device_info();
+    if (dev.sms <= 0) return KRON_ERR_CUDA;
+    if (plan->smem > dev.smem_per_block_optin) return KRON_ERR_NOT_SUPPORTED;
+    void* ws = noalloc_scratch();
+    if (!ws) return KRON_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    kron_status r = vl_upload(plan, ws, st);   // the shared array may hold another call's tables
+    if (r != KRON_OK) return r;
+    r = vl_fill_args(plan, X, Y, ws);
+    if (r != KRON_OK) return r;
+    void* fn = vl_kernel_ptr(plan->io);
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan->smem) != cudaSuccess)
+        return KRON_ERR_CUDA;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kVlThreads, plan->smem) != cudaSuccess)
+        return KRON_ERR_CUDA;
+    int grid = std::max(1, per_sm) * dev.sms;
+    grid = (int)std::min<size_t>((size_t)grid, plan->tiles.size());
+    int xbe = plan->xbuf_elems;
+    void* kargs[2] = {plan->args, &xbe};
+    if (cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(kVlThreads), kargs, plan->smem, st) != cudaSuccess)
+        return KRON_ERR_CUDA;
+    return KRON_OK;
+}
+
 KRON_API kron_status kron_varlen_plan_destroy(kron_varlen_plan* plan) {
     if (!plan) return KRON_OK;
     vl_drop_graph(plan);
