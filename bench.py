@@ -148,9 +148,29 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # our implementation
 # ---------------------------------------------------------------------------
+def rank_seed(seed, rank):
+    """Each rank draws its own batch (weak scaling: the work per GPU is fixed)."""
+    return seed + 1000 * rank
+
+
+def reduce_time_max(ms, dist, device):
+    """The step time of a multi-rank run is the slowest rank's (no data-path collective)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, units_per_rank, ms):
+    """Aggregate throughput: every rank's units over the slowest rank's time."""
+    return world * units_per_rank / (ms * 1e-3)
+
+
 def make_inputs(wl, rank=0):
     from paper_1304_7054_gb300 import inputs
-    b = inputs.make_batch(wl["kind"], wl["n"], wl["batch"], seed=wl["seed"] + 1000 * rank, x_dist="normal",
+    b = inputs.make_batch(wl["kind"], wl["n"], wl["batch"], seed=rank_seed(wl["seed"], rank), x_dist="normal",
                           dtype=np.float64 if wl["io"] == "f64" else np.float32)
     return b
 
@@ -374,15 +394,19 @@ def measure_varlen(kg, io, steps, warmup, torch, dev, peaks, count=200000, seed=
             else:
                 kg.kron3_batched(cs[0], cs[1], cs[2], gX, gY, ma=n, na=n, mb=n, nb=n, mc=n, nc=n, batch=cnt)
 
-    for _ in range(warmup):
-        per_size()
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(steps):
-        per_size()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms_ps = e0.elapsed_time(e1) / steps
+    try:
+        for _ in range(warmup):
+            per_size()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            per_size()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_ps = e0.elapsed_time(e1) / steps
+    except kg.KronError as e:
+        ms_ps = float("nan")
+        print(f"per-size launches failed: {e}", file=sys.stderr)
     plan.close()
     gbs = by / (ms * 1e-3) / 1e9
     return {"gflops": round(fl / (ms * 1e-3) / 1e9, 1), "hbm_gbs": round(gbs, 1),
@@ -432,15 +456,12 @@ def run_ours(args):
         sampler.start()
     total_ms, kern_ms = time_device(kg, b, X, Y, wl["compute"], args.steps, args.warmup, torch, sampler, dist)
     clocks = sampler.stop() if sampler else None
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = reduce_time_max(total_ms, dist, dev)
     err = sample_error(kg, b, Y, wl["io"], torch)
     ms = total_ms / args.steps
     fl = flops_per_instance(b.kind, b.n) * b.batch
     by = 2 * ESIZE[wl["io"]] * b.n ** b.kind * b.batch
-    value = world * fl / (ms * 1e-3) / 1e9
+    value = whole_job_rate(world, fl, ms) / 1e9
     kernel_name = kernel_of(b.kind, b.n, wl["io"], wl["compute"])
     achieved = by / (kern_ms * 1e-3) / 1e9
     del X, Y
@@ -494,6 +515,30 @@ def run_profile(args):
     import paper_1304_7054_gb300 as kg
     dev = torch.device("cuda", torch.cuda.current_device())
     kg.load_library()
+    if args.workload.startswith("varlen-"):
+        from paper_1304_7054_gb300 import inputs
+        io = args.workload.split("-", 1)[1]
+        v = inputs.make_varlen(args.batch or 200000, seed=5)
+        X = (torch.from_numpy(v.X) if io == "f32" else inputs.to_storage(v.X, io)).to(dev)
+        Y = torch.empty_like(X)
+        plan = kg.VarlenPlan([(k, n, *cs) for (k, n), cs in zip(v.classes, v.comps)], v.class_of, v.x_off,
+                             v.y_off, io=io)
+        ws = plan.alloc_workspace(dev)
+        for _ in range(args.warmup):
+            plan.execute(X, Y, ws)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(args.steps):
+            plan.execute(X, Y, ws)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        fl, by = varlen_stats(v, io)
+        print(json.dumps({"workload": args.workload, "instances": len(v.class_of), "kernel_ms": ms,
+                          "gflops": fl / (ms * 1e-3) / 1e9, "hbm_gbs": by / (ms * 1e-3) / 1e9}))
+        plan.close()
+        return
     wl = WORKLOADS[args.workload]
     b = make_inputs(wl)
     X = to_device_storage(b, wl["io"], torch, dev)
@@ -567,7 +612,7 @@ def main():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=HEADLINE)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["varlen-f32", "varlen-bf16"], default=HEADLINE)
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=8.0)
     ap.add_argument("--batch", type=int, default=0, help="override the batch (profiling a smaller case)")

@@ -173,7 +173,8 @@ KRON_API kron_status kron_autotune(kron_stream_t stream, int kind, int n, int64_
  * its operand starts at element offset h_x_off[p] of X and its result at
  * h_y_off[p] of Y; instances are contiguous (minimal leading dimensions),
  * alpha = 1, beta = 0.  Storage: KRON_R32F or KRON_R16BF / KRON_R16F
- * (components float).
+ * (components float).  X and Y may span at most 2^31 - 1 elements each
+ * (KRON_ERR_NOT_SUPPORTED beyond).
  *
  * kron_varlen_plan_create copies the host metadata, sorts instances by class,
  * chooses per-class tile sizes (from the tuning cache when present) and

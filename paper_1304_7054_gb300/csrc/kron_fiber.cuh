@@ -344,22 +344,30 @@ kron_status launch_fiber_n(const KronDesc& d, cudaStream_t st) {
     if (!a.err) return KRON_ERR_CUDA;
 
     // Instances per tile: about one fiber per thread and stage; bulk-copied tiles
-    // must be a multiple of 16 bytes.
-    int P = d.P > 0 ? d.P : (kFiberThreads + L::FPI - 1) / L::FPI;
+    // must be a multiple of 16 bytes.  If that rounding makes the tile too large
+    // for shared memory, the tile is loaded element by element instead.
+    const int P0 = d.P > 0 ? d.P : (kFiberThreads + L::FPI - 1) / L::FPI;
+    int P = P0;
+    int nstage = 0;
     if (d.contiguous) {
         const size_t ib = L::NX * sizeof(S);
         int mult = 1;
         while ((mult * ib) % 16) ++mult;
-        P = (P + mult - 1) / mult * mult;
+        P = (P0 + mult - 1) / mult * mult;
+        nstage = d.nstage >= 1 ? d.nstage : 3;
+        if (nstage > 8) nstage = 8;
     }
-    int nstage = 0;
-    if (d.contiguous) nstage = d.nstage >= 1 ? d.nstage : 3;
-    if (nstage > 8) nstage = 8;
     size_t smem = fiber_smem_bytes<T, S, N, D>(P, nstage);
     while (nstage > 1 && smem > dev.smem_per_block_optin) {
         --nstage;
         smem = fiber_smem_bytes<T, S, N, D>(P, nstage);
     }
+    if (smem > dev.smem_per_block_optin && nstage > 0) {
+        P = P0;
+        nstage = 0;
+        smem = fiber_smem_bytes<T, S, N, D>(P, nstage);
+    }
+    while (smem > dev.smem_per_block_optin && P > 1) smem = fiber_smem_bytes<T, S, N, D>(--P, nstage);
     if (smem > dev.smem_per_block_optin) return KRON_ERR_NOT_SUPPORTED;
     a.P = P;
     a.nstage = nstage;

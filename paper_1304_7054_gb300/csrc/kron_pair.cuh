@@ -127,7 +127,7 @@ struct PairLayout {
     // T (3-D): element (i, j, k, q) at i + N j + ST k + STQ q
     static constexpr int ST = stride_mod32(N * N, N);
     static constexpr int STQ = ST * N;
-    static constexpr int EX1 = (D == 2) ? SQ : STQ;
+    static constexpr int EX1 = (D == 2) ? 2 * SQ : STQ;   // 2-D: W double-buffered
     static constexpr int EX2 = (D == 2) ? 0 : SQ;
 };
 
@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(NT) pair_kernel(const __grid_constant__ PairAr
 #pragma unroll
                 for (int m = 0; m < N; ++m) x[m] = load_pair<S>(xr + N * m);
                 contract_dup<N>(a.da, x, w);
-                float* wr = ex1 + q * L::SQ + l;
+                float* wr = ex1 + (it & 1) * (size_t)P * L::SQ + q * L::SQ + l;
 #pragma unroll
                 for (int j = 0; j < N; ++j) *reinterpret_cast<f2*>(wr + L::SJ * j) = w[j];
             }
@@ -327,13 +327,19 @@ __global__ void __launch_bounds__(NT) pair_kernel(const __grid_constant__ PairAr
 
         S* Y = static_cast<S*>(a.Y);
         if constexpr (D == 2) {
+            const f2* m1p = reinterpret_cast<const f2*>(a.m1);
+            const float* wb = ex1 + (it & 1) * (size_t)P * L::SQ;
             const int F = cnt * N;
-            last_stage<S, N, D, NT>(a, F, [&](int f, float (&w)[N]) {
+            for (int f = tid; f < F; f += NT) {
                 const int q = f / N, j = f - q * N;
-                load_row<N>(ex1 + q * L::SQ + L::SJ * j, w);
-                return Y + (inst0 + q) * L::NX + N * j;
-            });
-            __syncthreads();   // ex1 is rewritten by the next tile's first stage
+                float w[N];
+                load_row<N>(wb + q * L::SQ + L::SJ * j, w);
+                f2 y[N / 2];
+                contract_rows<N>(m1p, w, y);
+                pair_store<S, N, D>(a, Y + (inst0 + q) * L::NX + N * j, y);
+            }
+            // W alternates between two buffers: the next tile's first stage writes the
+            // other one, and the barrier after it orders this tile's reads before reuse.
         } else {
             const int F = cnt * (N * N / 2);
             for (int u = tid; u < F; u += NT) {
@@ -410,7 +416,9 @@ kron_status launch_pair_n(const KronDesc& d, cudaStream_t st) {
         while ((mult * L::NX * sizeof(S)) % 16) ++mult;
         P = (P + mult - 1) / mult * mult;
     }
-    int nstage = d.nstage >= 1 ? d.nstage : 2;
+    // 2-D: one stage in flight gives the most resident CTAs, which matters more
+    // than a deeper pipeline (measured); 3-D: two stages.
+    int nstage = d.nstage >= 1 ? d.nstage : (D == 2 ? 1 : 2);
     if (nstage > 8) nstage = 8;
     size_t smem = pair_smem_bytes<S, N, D>(P, nstage);
     while (nstage > 1 && smem > dev.smem_per_block_optin) smem = pair_smem_bytes<S, N, D>(P, --nstage);

@@ -138,8 +138,8 @@ KRON_API kron_status kron_autotune(kron_stream_t stream, int kind, int n, int64_
     kron_get_tile_config(kind, n, io, comp, &def_P, &def_ns);
     std::vector<Entry> cands;
     const int base = kind == 2 ? (256 + n - 1) / n : (256 + n * n - 1) / (n * n);
-    for (int mul : {1, 2, 4})
-        for (int ns : {2, 3, 4}) cands.push_back(Entry{base * mul / 2 > 0 ? base * mul / 2 : 1, ns});
+    for (int mul : {1, 2, 3, 4})
+        for (int ns : {1, 2, 3}) cands.push_back(Entry{base * mul / 2 > 0 ? base * mul / 2 : 1, ns});
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return KRON_ERR_CUDA;
     float best = 1e30f;
@@ -151,7 +151,7 @@ KRON_API kron_status kron_autotune(kron_stream_t stream, int kind, int n, int64_
         for (int w = 0; w < 2 && ok; ++w) ok = run() == KRON_OK;
         if (!ok) continue;
         cudaEventRecord(e0, st);
-        for (int r = 0; r < 5; ++r) run();
+        for (int r = 0; r < 10; ++r) run();
         cudaEventRecord(e1, st);
         if (cudaEventSynchronize(e1) != cudaSuccess) { rs = KRON_ERR_CUDA; break; }
         float ms = 0;

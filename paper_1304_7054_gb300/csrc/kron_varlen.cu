@@ -66,9 +66,10 @@ __device__ __forceinline__ int vl_nx(int key) {
     return key < 16 ? n * n : n * n * n;
 }
 
-// Loads tile `td` into registers: element e = tid + kVlThreads * r.
+// Loads the operand elements of tile `td` into registers (element e = tid +
+// kVlThreads * r); xo[q] is the X offset of the tile's instance q (shared memory).
 template <typename S>
-__device__ __forceinline__ void vl_prefetch(const VarlenArgs& a, int4 td, S (&v)[kVlRegs]) {
+__device__ __forceinline__ void vl_prefetch(const VarlenArgs& a, int4 td, const int* xo, S (&v)[kVlRegs]) {
     const int nx = vl_nx(td.x);
     const unsigned inv = a.cls[td.x].inv;
     const int total = td.z * nx;
@@ -78,7 +79,7 @@ __device__ __forceinline__ void vl_prefetch(const VarlenArgs& a, int4 td, S (&v)
         const int e = threadIdx.x + kVlThreads * r;
         if (e < total) {
             const int q = nx == 1 ? e : (int)__umulhi((unsigned)e, inv);
-            v[r] = X[a.xoff[td.y + q] + (e - q * nx)];
+            v[r] = X[(int64_t)xo[q] + (e - q * nx)];
         }
     }
 }
@@ -96,8 +97,10 @@ __device__ __forceinline__ void vl_commit(int4 td, const S (&v)[kVlRegs], S* xt)
 // One tile of class (D, N): operand tile xt (linear, instance-major) -> outputs
 // back into xt (same layout), then copied to Y.
 template <typename S, int N, int D>
-__device__ __forceinline__ void vl_tile(const VarlenArgs& a, int4 td, S* xt, float* ex1, float* ex2) {
+__device__ __forceinline__ void vl_tile(const VarlenArgs& a, int4 td, S* xt, S* ot, float* ex1, float* ex2,
+                                        const int* yo) {
     using L = FiberLayout<N, D>;
+    constexpr int OSQ = (N + 1) * ipow(N, D - 1);   // padded output staging per instance
     const float* m1 = a.coef + vl_slot(D, N);
     const float* m2 = m1 + N * N;
     const float* m3 = m2 + N * N;
@@ -124,7 +127,7 @@ __device__ __forceinline__ void vl_tile(const VarlenArgs& a, int4 td, S* xt, flo
 #pragma unroll
             for (int l = 0; l < N; ++l) w[l] = wr[l];
             contract<N, float>(m1, w, y);
-            S* o = xt + q * L::NX + N * j;
+            S* o = ot + q * OSQ + (N + 1) * j;
 #pragma unroll
             for (int i = 0; i < N; ++i) o[i] = store_cvt<S, float>(y[i]);
         }
@@ -164,80 +167,114 @@ __device__ __forceinline__ void vl_tile(const VarlenArgs& a, int4 td, S* xt, flo
 #pragma unroll
             for (int l = 0; l < N; ++l) u[l] = ur[l];
             contract<N, float>(m1, u, y);
-            S* o = xt + q * L::NX + N * j + N * N * k;
+            S* o = ot + q * OSQ + (N + 1) * (j + N * k);
 #pragma unroll
             for (int i = 0; i < N; ++i) o[i] = store_cvt<S, float>(y[i]);
         }
     }
     __syncthreads();
-    // coalesced copy of the finished instances to Y
+    // coalesced copy of the finished instances to Y (the staging pads every
+    // mode-1 fiber to N + 1 elements, so the fiber writes above hit distinct banks)
     S* Y = static_cast<S*>(a.Y);
     const unsigned inv = a.cls[td.x].inv;
     for (int e = tid; e < cnt * L::NX; e += kVlThreads) {
         const int q = L::NX == 1 ? e : (int)__umulhi((unsigned)e, inv);
-        Y[a.yoff[td.y + q] + (e - q * L::NX)] = xt[e];
+        const int r = e - q * L::NX;
+        Y[(int64_t)yo[q] + r] = ot[q * OSQ + (N + 1) * (r / N) + r % N];
     }
 }
 
 template <typename S, int D>
-__device__ __forceinline__ void vl_dispatch_n(const VarlenArgs& a, int4 td, S* xt, float* ex1, float* ex2) {
+__device__ __forceinline__ void vl_dispatch_n(const VarlenArgs& a, int4 td, S* xt, S* ot, float* ex1, float* ex2,
+                                              const int* yo) {
     switch ((td.x & 15) + 1) {
-        case 1: vl_tile<S, 1, D>(a, td, xt, ex1, ex2); break;
-        case 2: vl_tile<S, 2, D>(a, td, xt, ex1, ex2); break;
-        case 3: vl_tile<S, 3, D>(a, td, xt, ex1, ex2); break;
-        case 4: vl_tile<S, 4, D>(a, td, xt, ex1, ex2); break;
-        case 5: vl_tile<S, 5, D>(a, td, xt, ex1, ex2); break;
-        case 6: vl_tile<S, 6, D>(a, td, xt, ex1, ex2); break;
-        case 7: vl_tile<S, 7, D>(a, td, xt, ex1, ex2); break;
-        case 8: vl_tile<S, 8, D>(a, td, xt, ex1, ex2); break;
-        case 9: vl_tile<S, 9, D>(a, td, xt, ex1, ex2); break;
-        case 10: vl_tile<S, 10, D>(a, td, xt, ex1, ex2); break;
-        case 11: vl_tile<S, 11, D>(a, td, xt, ex1, ex2); break;
-        case 12: vl_tile<S, 12, D>(a, td, xt, ex1, ex2); break;
-        case 13: vl_tile<S, 13, D>(a, td, xt, ex1, ex2); break;
-        case 14: vl_tile<S, 14, D>(a, td, xt, ex1, ex2); break;
-        case 15: vl_tile<S, 15, D>(a, td, xt, ex1, ex2); break;
-        case 16: vl_tile<S, 16, D>(a, td, xt, ex1, ex2); break;
+        case 1: vl_tile<S, 1, D>(a, td, xt, ot, ex1, ex2, yo); break;
+        case 2: vl_tile<S, 2, D>(a, td, xt, ot, ex1, ex2, yo); break;
+        case 3: vl_tile<S, 3, D>(a, td, xt, ot, ex1, ex2, yo); break;
+        case 4: vl_tile<S, 4, D>(a, td, xt, ot, ex1, ex2, yo); break;
+        case 5: vl_tile<S, 5, D>(a, td, xt, ot, ex1, ex2, yo); break;
+        case 6: vl_tile<S, 6, D>(a, td, xt, ot, ex1, ex2, yo); break;
+        case 7: vl_tile<S, 7, D>(a, td, xt, ot, ex1, ex2, yo); break;
+        case 8: vl_tile<S, 8, D>(a, td, xt, ot, ex1, ex2, yo); break;
+        case 9: vl_tile<S, 9, D>(a, td, xt, ot, ex1, ex2, yo); break;
+        case 10: vl_tile<S, 10, D>(a, td, xt, ot, ex1, ex2, yo); break;
+        case 11: vl_tile<S, 11, D>(a, td, xt, ot, ex1, ex2, yo); break;
+        case 12: vl_tile<S, 12, D>(a, td, xt, ot, ex1, ex2, yo); break;
+        case 13: vl_tile<S, 13, D>(a, td, xt, ot, ex1, ex2, yo); break;
+        case 14: vl_tile<S, 14, D>(a, td, xt, ot, ex1, ex2, yo); break;
+        case 15: vl_tile<S, 15, D>(a, td, xt, ot, ex1, ex2, yo); break;
+        case 16: vl_tile<S, 16, D>(a, td, xt, ot, ex1, ex2, yo); break;
     }
 }
 
 template <typename S>
 __global__ void __launch_bounds__(kVlThreads) varlen_kernel(const __grid_constant__ VarlenArgs a, int xbuf_elems) {
     extern __shared__ __align__(128) unsigned char smem[];
-    S* xb0 = reinterpret_cast<S*>(smem);
+    // Offsets of the instances of three consecutive tiles of this CTA (a ring):
+    // X offsets then Y offsets, kVlThreads each (a tile has at most that many).
+    int* ring = reinterpret_cast<int*>(smem);
+    S* xb0 = reinterpret_cast<S*>(smem + 6 * kVlThreads * sizeof(int));
     S* xb1 = xb0 + xbuf_elems;
-    float* ex1 = reinterpret_cast<float*>(smem + round_up(2 * (size_t)xbuf_elems * sizeof(S), 128));
-    // ex2 follows ex1; its offset depends on the class, see vl_smem_split
+    float* ex1 = reinterpret_cast<float*>(
+        smem + round_up(6 * kVlThreads * sizeof(int) + 2 * (size_t)xbuf_elems * sizeof(S), 128));
     const int G = gridDim.x;
-    int tile = blockIdx.x;
-    if (tile >= a.ntiles) return;
-    S v[kVlRegs];
-    int4 td = a.tiles[tile];
-    vl_prefetch<S>(a, td, v);
-    vl_commit<S>(td, v, xb0);
+    const int tid = threadIdx.x;
+    const int t0 = blockIdx.x;
+    if (t0 >= a.ntiles) return;
+    const int4 none = make_int4(0, 0, 0, 0);
+    // Pipeline: descriptors are read two tiles ahead, instance offsets one tile
+    // ahead (through the ring), operand elements one tile ahead (registers), so no
+    // global load is waited for at the start of a tile.
+    int4 d0 = a.tiles[t0];
+    int4 d1 = t0 + G < a.ntiles ? a.tiles[t0 + G] : none;
+    int4 d2 = t0 + 2 * G < a.ntiles ? a.tiles[t0 + 2 * G] : none;
+    if (tid < d0.z) {
+        ring[tid] = (int)a.xoff[d0.y + tid];
+        ring[kVlThreads + tid] = (int)a.yoff[d0.y + tid];
+    }
+    if (tid < d1.z) {
+        ring[2 * kVlThreads + tid] = (int)a.xoff[d1.y + tid];
+        ring[3 * kVlThreads + tid] = (int)a.yoff[d1.y + tid];
+    }
     __syncthreads();
-    for (int it = 0; tile < a.ntiles; ++it, tile += G) {
+    S v[kVlRegs];
+    vl_prefetch<S>(a, d0, ring, v);
+    vl_commit<S>(d0, v, xb0);
+    __syncthreads();
+    int it = 0;
+    for (int tile = t0; tile < a.ntiles; ++it, tile += G) {
         S* xt = (it & 1) ? xb1 : xb0;
         S* xn = (it & 1) ? xb0 : xb1;
-        const int next = tile + G;
-        int4 tn = make_int4(0, 0, 0, 0);
-        if (next < a.ntiles) {
-            tn = a.tiles[next];
-            vl_prefetch<S>(a, tn, v);
+        const int s0 = it % 3, s1 = (it + 1) % 3, s2 = (it + 2) % 3;
+        // offsets of tile + 2G, stored at the end of this tile
+        int xo2 = 0, yo2 = 0;
+        if (tid < d2.z) {
+            xo2 = (int)a.xoff[d2.y + tid];
+            yo2 = (int)a.yoff[d2.y + tid];
         }
-        const int key = td.x;
+        const int4 d3 = tile + 3 * G < a.ntiles ? a.tiles[tile + 3 * G] : none;
+        if (d1.z) vl_prefetch<S>(a, d1, ring + 2 * kVlThreads * s1, v);
+        const int key = d0.x;
         const int P = a.cls[key].P;
         const int n = (key & 15) + 1;
         // exchange buffer 2 starts after P * (per-instance size of buffer 1)
-        float* ex2 = ex1 + (size_t)P * (key < 16 ? stride_mod32(n * n + n - 1, n)
-                                                 : stride_mod32(n * n, n) * n);
+        float* ex2 = ex1 + (size_t)P * (key < 16 ? stride_mod32(n * n + n - 1, n) : stride_mod32(n * n, n) * n);
+        const int* yo = ring + 2 * kVlThreads * s0 + kVlThreads;
+        // the last contraction stages its outputs in the other operand buffer
         if (key < 16)
-            vl_dispatch_n<S, 2>(a, td, xt, ex1, ex2);
+            vl_dispatch_n<S, 2>(a, d0, xt, xn, ex1, ex2, yo);
         else
-            vl_dispatch_n<S, 3>(a, td, xt, ex1, ex2);
-        if (next < a.ntiles) vl_commit<S>(tn, v, xn);
+            vl_dispatch_n<S, 3>(a, d0, xt, xn, ex1, ex2, yo);
+        __syncthreads();   // outputs copied out before the next tile lands in xn
+        if (d1.z) vl_commit<S>(d1, v, xn);
+        if (tid < d2.z) {
+            ring[2 * kVlThreads * s2 + tid] = xo2;
+            ring[2 * kVlThreads * s2 + kVlThreads + tid] = yo2;
+        }
         __syncthreads();
-        td = tn;
+        d0 = d1;
+        d1 = d2;
+        d2 = d3;
     }
 }
 
@@ -256,6 +293,7 @@ static int vl_default_P(int kind, int n) {
     const int nx = kind == 2 ? n * n : n * n * n;
     int P = std::max(1, (kVlThreads + fpi - 1) / fpi);
     P = std::min(P, kVlMaxTile / nx);
+    P = std::min(P, kVlThreads);
     return std::max(1, P);
 }
 
@@ -326,14 +364,14 @@ static kron_status vl_build(kron_varlen_plan* p) {
             const int c = (int)std::min<int64_t>(P, cnt - s);
             tl.push_back(T{flops * c, make_int4(key, (int)(start + s), c, 0)});
         }
-        max_x = std::max(max_x, (size_t)P * nx);
+        max_x = std::max(max_x, (size_t)P * (nx / n) * (n + 1));   // padded output staging
         max_smem_rest = std::max(max_smem_rest, vl_ex_floats(kind, n, P) * sizeof(float));
     }
     if (p->order.size() > (size_t)INT32_MAX) return KRON_ERR_NOT_SUPPORTED;
     std::stable_sort(tl.begin(), tl.end(), [](const T& a, const T& b) { return a.work > b.work; });
     for (const T& t : tl) p->tiles.push_back(t.td);
     p->xbuf_elems = (int)round_up(max_x, 64);
-    p->smem = round_up(2 * (size_t)p->xbuf_elems * es, 128) + max_smem_rest;
+    p->smem = round_up(6 * kVlThreads * sizeof(int) + 2 * (size_t)p->xbuf_elems * es, 128) + max_smem_rest;
     // Sized for one tile per instance (the most any tile size can give), so that
     // re-tuning never outgrows a workspace sized before it.
     p->ws_bytes = round_up(p->order.size() * sizeof(int4), 256) + 2 * round_up(p->order.size() * 8, 256);
@@ -495,7 +533,7 @@ KRON_API kron_status kron_varlen_plan_create(kron_varlen_plan** plan, int num_cl
         int tp = 0, td = 0;
         kron_get_tile_config(d.kind, n, io, (kron_compute)kVarlenTag, &tp, &td);
         const int nx = d.kind == 2 ? nn : nn * n;
-        p->P[key] = (tp > 0 && tp * nx <= kVlMaxTile) ? tp : vl_default_P(d.kind, n);
+        p->P[key] = (tp > 0 && tp * nx <= kVlMaxTile && tp <= kVlThreads) ? tp : vl_default_P(d.kind, n);
     }
     p->cls_of.resize(batch_count);
     p->xoff.assign(h_x_off, h_x_off + batch_count);
@@ -528,6 +566,10 @@ KRON_API kron_status kron_varlen_plan_create(kron_varlen_plan** plan, int num_cl
                 kron_varlen_plan_destroy(p);
                 return KRON_ERR_INVALID_VALUE;
             }
+    }
+    if (xt >= INT32_MAX || yt >= INT32_MAX) {   // the kernel keeps element offsets in 32 bits
+        kron_varlen_plan_destroy(p);
+        return KRON_ERR_NOT_SUPPORTED;
     }
     p->x_total = xt;
     p->y_total = yt;
@@ -604,7 +646,7 @@ KRON_API kron_status kron_varlen_tune(kron_varlen_plan* plan, const void* X, voi
         const int key = work[w].second;
         const int kind = key < 16 ? 2 : 3, n = (key & 15) + 1;
         const int nx = kind == 2 ? n * n : n * n * n;
-        const int pmax = std::max(1, kVlMaxTile / nx);
+        const int pmax = std::max(1, std::min(kVlThreads, kVlMaxTile / nx));
         const int cur = plan->P[key];
         int best_P = cur;
         for (int cand : {cur / 2, cur * 2, cur * 4, cur / 4, cur + cur / 2}) {

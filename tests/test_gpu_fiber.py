@@ -80,7 +80,7 @@ def test_all_sizes(kind, n, io):
 
 
 @pytest.mark.parametrize("io", ["bf16", "f16"])
-@pytest.mark.parametrize("n", [1, 3, 4, 5, 8, 10, 12, 16])
+@pytest.mark.parametrize("n", list(range(1, 17)))
 @pytest.mark.parametrize("kind", [2, 3])
 def test_16bit_storage(kind, n, io):
     batch = 777 if kind == 2 else 65
