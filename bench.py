@@ -426,7 +426,7 @@ def traffic_for(kernel_name):
     if not e:
         return None
     from paper_1304_7054_gb300 import build as lb
-    if e.get("source_hash") != lb.source_hash():
+    if e.get("source_hash") != lb.source_hash(kernel_name.split("<")[0]):
         return None
     return e.get("dram_bytes_per_launch")
 

@@ -72,11 +72,24 @@ if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
 
 
-def source_hash() -> str:
-    """Hash of the kernel sources (used to tell whether a stored profile still applies)."""
+# Sources that define each kernel family (its device code, launcher and dispatch).
+FAMILY_SOURCES = {
+    "pair_kernel": ["kron_pair.cuh", "kron_fiber.cuh", "kron_device.cuh", "kron_internal.h", "kron_api.cu"],
+    "fiber_kernel": ["kron_fiber.cuh", "kron_device.cuh", "kron_internal.h", "kron_api.cu"],
+    "tc2_kernel": ["kron_tc.cu", "kron_fiber.cuh", "kron_device.cuh", "kron_internal.h", "kron_api.cu"],
+    "tc3_kernel": ["kron_tc.cu", "kron_fiber.cuh", "kron_device.cuh", "kron_internal.h", "kron_api.cu"],
+    "varlen_kernel": ["kron_varlen.cu", "kron_fiber.cuh", "kron_device.cuh", "kron_internal.h"],
+}
+
+
+def source_hash(family: str | None = None) -> str:
+    """Hash of the sources of one kernel family (all sources if None); a stored
+    profile applies only while this hash is unchanged."""
     import hashlib
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(CSRC, "*"))):
+    files = ([os.path.join(CSRC, f) for f in FAMILY_SOURCES[family]] if family
+             else sorted(glob.glob(os.path.join(CSRC, "*"))))
+    for f in files:
         h.update(os.path.basename(f).encode())
         h.update(open(f, "rb").read())
     return h.hexdigest()[:16]
