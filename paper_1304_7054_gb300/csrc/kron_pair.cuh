@@ -112,7 +112,7 @@ struct PairArgs {
     unsigned* err;
 };
 
-template <int N, int D>
+template <int N, int D, int SB>
 struct PairLayout {
     static_assert(N % 2 == 0, "pair kernels need an even N");
     static constexpr int NX = ipow(N, D);
@@ -124,10 +124,16 @@ struct PairLayout {
     static constexpr int SJ = N + 2;
     static constexpr int SK = stride_mod32(SJ * (N - 1) + N, N);
     static constexpr int SQ = (D == 2) ? SK : SK * N;
-    // T (3-D): element (i, j, k, q) at i + N j + ST k + STQ q
-    static constexpr int ST = stride_mod32(N * N, N);
+    // T (3-D): element (i, j, k, q) at i + N j + ST k + STQ q.  With FP32 storage T
+    // overwrites the operand tile in place (ST = N^2): every thread reads its two
+    // fibers into registers before it writes the two output fibers at the same
+    // addresses, and no other thread touches them.  That saves a buffer, so more
+    // CTAs are resident; the tile is refilled after stage B instead of stage A.
+    static constexpr bool TIN = (D == 3 && SB == 4);
+    static constexpr int ST = TIN ? N * N : stride_mod32(N * N, N);
     static constexpr int STQ = ST * N;
-    static constexpr int EX1 = (D == 2) ? 2 * SQ : STQ;   // 2-D: W double-buffered
+    // 2-D: W double-buffered; 3-D: T in its own buffer unless it is in place
+    static constexpr int EX1 = (D == 2) ? 2 * SQ : (TIN ? 0 : STQ);
     static constexpr int EX2 = (D == 2) ? 0 : SQ;
 };
 
@@ -135,7 +141,7 @@ struct PairLayout {
 template <typename S, int N, int D>
 __device__ __forceinline__ void pair_issue(const PairArgs<N, D>& a, void* dst, uint64_t* bar, int64_t tile,
                                            uint64_t pol) {
-    using L = PairLayout<N, D>;
+    using L = PairLayout<N, D, (int)sizeof(S)>;
     const int lane = threadIdx.x & 31;
     const int64_t inst0 = tile * a.P;
     const int cnt = (int)min((int64_t)a.P, a.batch - inst0);
@@ -236,7 +242,7 @@ __device__ __forceinline__ void last_stage(const PairArgs<N, D>& a, int F, Fetch
 
 template <typename S, int N, int D, int NT>
 __global__ void __launch_bounds__(NT) pair_kernel(const __grid_constant__ PairArgs<N, D> a) {
-    using L = PairLayout<N, D>;
+    using L = PairLayout<N, D, (int)sizeof(S)>;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
     const int P = a.P;
@@ -304,7 +310,7 @@ __global__ void __launch_bounds__(NT) pair_kernel(const __grid_constant__ PairAr
 #pragma unroll
                 for (int p = 0; p < N; ++p) x[p] = load_pair<S>(xr + N * N * p);
                 contract_dup<N>(a.da, x, t);
-                float* tr = ex1 + q * L::STQ + i + N * j;
+                float* tr = (L::TIN ? reinterpret_cast<float*>(xt) : ex1) + q * L::STQ + i + N * j;
 #pragma unroll
                 for (int k = 0; k < N; ++k) *reinterpret_cast<f2*>(tr + L::ST * k) = t[k];
             }
@@ -317,11 +323,13 @@ __global__ void __launch_bounds__(NT) pair_kernel(const __grid_constant__ PairAr
             }
             return;
         }
-        if (warp0) {
-            const int64_t next = tile + a.nstage * grid;
-            if (next < ntiles) {
-                fence_proxy_async_smem();
-                pair_issue<S, N, D>(a, xt, &bars[s], next, pol);
+        if constexpr (!L::TIN) {
+            if (warp0) {
+                const int64_t next = tile + a.nstage * grid;
+                if (next < ntiles) {
+                    fence_proxy_async_smem();
+                    pair_issue<S, N, D>(a, xt, &bars[s], next, pol);
+                }
             }
         }
 
@@ -345,7 +353,7 @@ __global__ void __launch_bounds__(NT) pair_kernel(const __grid_constant__ PairAr
             for (int u = tid; u < F; u += NT) {
                 const int q = u / (N * N / 2), r = u - q * (N * N / 2);
                 const int i = 2 * (r % (N / 2)), k = r / (N / 2);
-                const float* tr = ex1 + q * L::STQ + i + L::ST * k;
+                const float* tr = (L::TIN ? reinterpret_cast<const float*>(xt) : ex1) + q * L::STQ + i + L::ST * k;
                 f2 t[N], v[N];
 #pragma unroll
                 for (int m = 0; m < N; ++m) t[m] = *reinterpret_cast<const f2*>(tr + N * m);
@@ -355,13 +363,35 @@ __global__ void __launch_bounds__(NT) pair_kernel(const __grid_constant__ PairAr
                 for (int j = 0; j < N; ++j) *reinterpret_cast<f2*>(ur + L::SJ * j) = v[j];
             }
             __syncthreads();
+            if constexpr (L::TIN) {
+                if (warp0) {   // T is consumed: the tile buffer takes the next operands
+                    const int64_t next = tile + a.nstage * grid;
+                    if (next < ntiles) {
+                        fence_proxy_async_smem();
+                        pair_issue<S, N, D>(a, xt, &bars[s], next, pol);
+                    }
+                }
+            }
             const int F3 = cnt * N * N;
-            last_stage<S, N, D, NT>(a, F3, [&](int f, float (&u)[N]) {
-                const int q = f / (N * N), r = f - q * (N * N);
-                const int j = r % N, k = r / N;
-                load_row<N>(ex2 + q * L::SQ + L::SJ * j + L::SK * k, u);
-                return Y + (inst0 + q) * L::NX + N * j + N * N * k;
-            });
+            if constexpr (N >= 14) {   // two fibers per step: more ILP (measured faster at n = 16)
+                last_stage<S, N, D, NT>(a, F3, [&](int f, float (&u)[N]) {
+                    const int q = f / (N * N), r = f - q * (N * N);
+                    const int j = r % N, k = r / N;
+                    load_row<N>(ex2 + q * L::SQ + L::SJ * j + L::SK * k, u);
+                    return Y + (inst0 + q) * L::NX + N * j + N * N * k;
+                });
+            } else {                   // one fiber per step: fewer registers (faster at n = 10)
+                const f2* m1p = reinterpret_cast<const f2*>(a.m1);
+                for (int f = tid; f < F3; f += NT) {
+                    const int q = f / (N * N), r = f - q * (N * N);
+                    const int j = r % N, k = r / N;
+                    float u[N];
+                    load_row<N>(ex2 + q * L::SQ + L::SJ * j + L::SK * k, u);
+                    f2 y[N / 2];
+                    contract_rows<N>(m1p, u, y);
+                    pair_store<S, N, D>(a, Y + (inst0 + q) * L::NX + N * j + N * N * k, y);
+                }
+            }
             // ex2 is rewritten only after the next tile's first barrier.
         }
     }
@@ -369,7 +399,7 @@ __global__ void __launch_bounds__(NT) pair_kernel(const __grid_constant__ PairAr
 
 template <typename S, int N, int D>
 size_t pair_smem_bytes(int P, int nstage) {
-    using L = PairLayout<N, D>;
+    using L = PairLayout<N, D, (int)sizeof(S)>;
     return 128 + nstage * round_up((size_t)P * L::SX * sizeof(S), 128) + (size_t)P * (L::EX1 + L::EX2) * sizeof(float);
 }
 
@@ -383,7 +413,7 @@ struct PairConfig {
 
 template <typename S, int N, int D>
 kron_status launch_pair_n(const KronDesc& d, cudaStream_t st) {
-    using L = PairLayout<N, D>;
+    using L = PairLayout<N, D, (int)sizeof(S)>;
     constexpr int NT = PairConfig<N, D>::NT;
     const DeviceInfo& dev = device_info();
     if (dev.sms <= 0) return KRON_ERR_CUDA;
@@ -416,9 +446,9 @@ kron_status launch_pair_n(const KronDesc& d, cudaStream_t st) {
         while ((mult * L::NX * sizeof(S)) % 16) ++mult;
         P = (P + mult - 1) / mult * mult;
     }
-    // 2-D: one stage in flight gives the most resident CTAs, which matters more
-    // than a deeper pipeline (measured); 3-D: two stages.
-    int nstage = d.nstage >= 1 ? d.nstage : (D == 2 ? 1 : 2);
+    // One stage in flight gives the most resident CTAs, which matters more than a
+    // deeper pipeline (measured for both kinds).
+    int nstage = d.nstage >= 1 ? d.nstage : 1;
     if (nstage > 8) nstage = 8;
     size_t smem = pair_smem_bytes<S, N, D>(P, nstage);
     while (nstage > 1 && smem > dev.smem_per_block_optin) smem = pair_smem_bytes<S, N, D>(P, --nstage);

@@ -8,12 +8,16 @@
 // has a compile-time body -- the same sum factorisation as the fixed-size
 // CUDA-core kernels (paper Sec. 2.1, Algorithm 1's modes with the intermediates
 // on chip) -- and its components sit at a fixed slot of the parameter bank, so
-// each FMA reads its coefficient as a constant operand.
+// each FMA reads its coefficients as a constant operand.  Every contraction is
+// done in packed pairs of output rows (fma.rn.f32x2 with the coefficient pair
+// (M[i,l], M[i+1,l]) and the operand duplicated), so each stage writes its
+// outputs as adjacent pairs; rows are padded to an even count.
 //
 // Data flow per CTA: the operand elements of the next tile are loaded into
 // registers (any alignment, coalesced) while the current tile is contracted in
-// shared memory; the last contraction writes its fibers into the free operand
-// buffer, from which consecutive threads copy the outputs to Y (coalesced).
+// shared memory; the last contraction writes its fibers into the operand buffer
+// (dead after the first contraction), from which consecutive threads copy the
+// outputs to Y (coalesced); then the next tile is committed to that buffer.
 //
 // Workspace (caller-owned device memory, written on the first execute with a
 // given pointer): tile table (int4: class key, first sorted index, count, 0),
@@ -28,6 +32,7 @@
 #include "kron_device.cuh"
 #include "kron_fiber.cuh"
 #include "kron_internal.h"
+#include "kron_pair.cuh"
 
 namespace kron {
 
@@ -37,20 +42,29 @@ constexpr int kVlMaxTile = kVlThreads * kVlRegs;       // elements per tile
 constexpr int kVlKeys = 32;                            // class key = 16 (kind - 2) + n - 1
 
 __host__ __device__ constexpr int sq_sum(int n) { return (n - 1) * n * (2 * n - 1) / 6; }   // sum k^2, k < n
-// Parameter-bank slot of class (kind, n): 2-D classes hold M1, M2, 3-D classes
-// M1, M2, M3, each n x n column-major.
+// Rows of a component padded to an even count, and the sum over k < n of
+// pad(k) * k (the odd k < n add k each: (n/2)^2 in total).
+__host__ __device__ constexpr int vl_rows(int n) { return n + (n & 1); }
+__host__ __device__ constexpr int vl_psum(int n) { return sq_sum(n) + (n / 2) * (n / 2); }
+// Parameter-bank slot (floats) of class (kind, n): 2-D classes hold M1, M2, 3-D
+// classes M1, M2, M3, each vl_rows(n) x n column-major with zero padding rows.
 __host__ __device__ constexpr int vl_slot(int kind, int n) {
-    return kind == 2 ? 2 * sq_sum(n) : 2 * sq_sum(17) + 3 * sq_sum(n);
+    return kind == 2 ? 2 * vl_psum(n) : 2 * vl_psum(17) + 3 * vl_psum(n);
 }
-constexpr int kVlCoef = 2 * sq_sum(17) + 3 * sq_sum(17);   // 7480 floats
+constexpr int kVlCoef = 2 * vl_psum(17) + 3 * vl_psum(17);   // 7800 floats
+// Padded row length of the exchange buffers: even (64-bit pair stores) and
+// 2 mod 4, so that lanes a row apart hit distinct banks.
+__host__ __device__ constexpr int vl_kp(int n) {
+    return vl_rows(n) + ((vl_rows(n) % 4 == 2) ? 0 : 2);
+}
 
 struct VlClass {
     int P;              // instances per tile (0 = class absent)
     unsigned inv;       // ceil(2^32 / n^kind): exact quotient e / n^kind for e < 4096
 };
 
-struct VarlenArgs {
-    float coef[kVlCoef];
+struct __align__(8) VarlenArgs {
+    float coef[kVlCoef];      // 8-byte aligned: read as coefficient pairs
     VlClass cls[kVlKeys];
     const int4* tiles;
     const int64_t* xoff;
@@ -60,6 +74,8 @@ struct VarlenArgs {
     int ntiles;
     unsigned* err;
 };
+
+static_assert(sizeof(VarlenArgs) <= 32764, "kernel parameter space");
 
 __device__ __forceinline__ int vl_nx(int key) {
     const int n = (key & 15) + 1;
@@ -94,93 +110,131 @@ __device__ __forceinline__ void vl_commit(int4 td, const S (&v)[kVlRegs], S* xt)
     }
 }
 
-// One tile of class (D, N): operand tile xt (linear, instance-major) -> outputs
-// back into xt (same layout), then copied to Y.
+// Packed-pair contraction of one fiber: (y[2r], y[2r+1]) = M[2r:2r+2, :] x, with
+// M stored as vl_rows(N) x N (column-major, read as coefficient pairs).
+template <int N>
+__device__ __forceinline__ void vl_contract(const float* M, const float (&x)[N], f2 (&y)[vl_rows(N) / 2]) {
+    constexpr int R = vl_rows(N) / 2;
+    const f2* Mp = reinterpret_cast<const f2*>(M);
+    const f2 x0 = f2_pack(x[0], x[0]);
+#pragma unroll
+    for (int r = 0; r < R; ++r) y[r] = fmul2(Mp[r], x0);
+#pragma unroll
+    for (int l = 1; l < N; ++l) {
+        const f2 xl = f2_pack(x[l], x[l]);
+#pragma unroll
+        for (int r = 0; r < R; ++r) y[r] = ffma2(Mp[r + R * l], xl, y[r]);
+    }
+}
+
+// Stores output pairs (rows 2r, 2r+1) at dst[2r] (float, 8-byte aligned).
+template <int N>
+__device__ __forceinline__ void vl_store_pairs(float* dst, const f2 (&y)[vl_rows(N) / 2]) {
+#pragma unroll
+    for (int r = 0; r < vl_rows(N) / 2; ++r) *reinterpret_cast<f2*>(dst + 2 * r) = y[r];
+}
+
+// Output pairs rounded to the storage type, staged at dst[2r].
+template <typename S, int N>
+__device__ __forceinline__ void vl_stage_out(S* dst, const f2 (&y)[vl_rows(N) / 2]) {
+    if constexpr (sizeof(S) == 4) {
+#pragma unroll
+        for (int r = 0; r < vl_rows(N) / 2; ++r) *reinterpret_cast<f2*>(dst + 2 * r) = y[r];
+    } else {
+#pragma unroll
+        for (int r = 0; r < vl_rows(N) / 2; ++r) *reinterpret_cast<unsigned*>(dst + 2 * r) = pack16<S>(y[r]);
+    }
+}
+
+// One tile of class (D, N).  Operand tile xt: instance-major, column-major inside
+// (linear).  Exchange layouts put each stage's output pairs next to each other:
+//   2-D   W(l, j)    at j + KP l                 (stage 1 writes pairs along j)
+//   3-D   T(i, j, k) at k + KP i + KP N j        (stage A: pairs along k)
+//         U(i, j, k) at j + KP k + KP N i        (stage B: pairs along j)
+//   out   Y(i, j, k) at i + KP (j + N k)         (last stage: pairs along i)
+// The outputs are staged in the other operand buffer `ot` and copied to Y by
+// consecutive threads.
 template <typename S, int N, int D>
 __device__ __forceinline__ void vl_tile(const VarlenArgs& a, int4 td, S* xt, S* ot, float* ex1, float* ex2,
                                         const int* yo) {
-    using L = FiberLayout<N, D>;
-    constexpr int OSQ = (N + 1) * ipow(N, D - 1);   // padded output staging per instance
+    constexpr int NX = ipow(N, D);
+    constexpr int KP = vl_kp(N);
+    constexpr int R = vl_rows(N) / 2;
+    constexpr int EXQ = KP * ipow(N, D - 1);   // exchange / staging elements per instance
     const float* m1 = a.coef + vl_slot(D, N);
-    const float* m2 = m1 + N * N;
-    const float* m3 = m2 + N * N;
+    const float* m2 = m1 + vl_rows(N) * N;
+    const float* m3 = m2 + vl_rows(N) * N;
     const int cnt = td.z;
     const int tid = threadIdx.x;
     if constexpr (D == 2) {
         const int F = cnt * N;
-        for (int f = tid; f < F; f += kVlThreads) {
+        for (int f = tid; f < F; f += kVlThreads) {   // stage 1: mode 2, fibers (l, q)
             const int q = f / N, l = f - q * N;
-            const S* xr = xt + q * L::NX + l;
-            float x[N], w[N];
+            const S* xr = xt + q * NX + l;
+            float x[N];
 #pragma unroll
             for (int m = 0; m < N; ++m) x[m] = load_cvt<float, S>(xr[N * m]);
-            contract<N, float>(m2, x, w);
-            float* wr = ex1 + q * L::SUQ + l;
-#pragma unroll
-            for (int j = 0; j < N; ++j) wr[(N + 1) * j] = w[j];
+            f2 w[R];
+            vl_contract<N>(m2, x, w);
+            vl_store_pairs<N>(ex1 + q * EXQ + KP * l, w);
         }
         __syncthreads();
-        for (int f = tid; f < F; f += kVlThreads) {
+        for (int f = tid; f < F; f += kVlThreads) {   // stage 2: mode 1, fibers (j, q)
             const int q = f / N, j = f - q * N;
-            const float* wr = ex1 + q * L::SUQ + (N + 1) * j;
-            float w[N], y[N];
+            const float* wr = ex1 + q * EXQ + j;
+            float w[N];
 #pragma unroll
-            for (int l = 0; l < N; ++l) w[l] = wr[l];
-            contract<N, float>(m1, w, y);
-            S* o = ot + q * OSQ + (N + 1) * j;
-#pragma unroll
-            for (int i = 0; i < N; ++i) o[i] = store_cvt<S, float>(y[i]);
+            for (int l = 0; l < N; ++l) w[l] = wr[KP * l];
+            f2 y[R];
+            vl_contract<N>(m1, w, y);
+            vl_stage_out<S, N>(ot + q * EXQ + KP * j, y);
         }
     } else {
         const int F = cnt * N * N;
-        for (int f = tid; f < F; f += kVlThreads) {
+        for (int f = tid; f < F; f += kVlThreads) {   // stage A: mode 3, fibers (i, j)
             const int q = f / (N * N), r = f - q * (N * N);
             const int i = r % N, j = r / N;
-            const S* xr = xt + q * L::NX + i + N * j;
-            float x[N], t[N];
+            const S* xr = xt + q * NX + i + N * j;
+            float x[N];
 #pragma unroll
             for (int p = 0; p < N; ++p) x[p] = load_cvt<float, S>(xr[N * N * p]);
-            contract<N, float>(m3, x, t);
-            float* tr = ex1 + q * L::STQ + i + N * j;
-#pragma unroll
-            for (int k = 0; k < N; ++k) tr[L::ST * k] = t[k];
+            f2 t[R];
+            vl_contract<N>(m3, x, t);
+            vl_store_pairs<N>(ex1 + q * EXQ + KP * i + KP * N * j, t);
         }
         __syncthreads();
-        for (int f = tid; f < F; f += kVlThreads) {
+        for (int f = tid; f < F; f += kVlThreads) {   // stage B: mode 2, fibers (i, k)
             const int q = f / (N * N), r = f - q * (N * N);
-            const int i = r % N, k = r / N;
-            const float* tr = ex1 + q * L::STQ + i + L::ST * k;
-            float t[N], u[N];
+            const int k = r % N, i = r / N;
+            const float* tr = ex1 + q * EXQ + k + KP * i;
+            float t[N];
 #pragma unroll
-            for (int m = 0; m < N; ++m) t[m] = tr[N * m];
-            contract<N, float>(m2, t, u);
-            float* ur = ex2 + q * L::SUQ + i + L::SU * k;
-#pragma unroll
-            for (int j = 0; j < N; ++j) ur[(N + 1) * j] = u[j];
+            for (int m = 0; m < N; ++m) t[m] = tr[KP * N * m];
+            f2 u[R];
+            vl_contract<N>(m2, t, u);
+            vl_store_pairs<N>(ex2 + q * EXQ + KP * k + KP * N * i, u);
         }
         __syncthreads();
-        for (int f = tid; f < F; f += kVlThreads) {
+        for (int f = tid; f < F; f += kVlThreads) {   // stage C: mode 1, fibers (j, k)
             const int q = f / (N * N), r = f - q * (N * N);
             const int j = r % N, k = r / N;
-            const float* ur = ex2 + q * L::SUQ + (N + 1) * j + L::SU * k;
-            float u[N], y[N];
+            const float* ur = ex2 + q * EXQ + j + KP * k;
+            float u[N];
 #pragma unroll
-            for (int l = 0; l < N; ++l) u[l] = ur[l];
-            contract<N, float>(m1, u, y);
-            S* o = ot + q * OSQ + (N + 1) * (j + N * k);
-#pragma unroll
-            for (int i = 0; i < N; ++i) o[i] = store_cvt<S, float>(y[i]);
+            for (int l = 0; l < N; ++l) u[l] = ur[KP * N * l];
+            f2 y[R];
+            vl_contract<N>(m1, u, y);
+            vl_stage_out<S, N>(ot + q * EXQ + KP * (j + N * k), y);
         }
     }
     __syncthreads();
-    // coalesced copy of the finished instances to Y (the staging pads every
-    // mode-1 fiber to N + 1 elements, so the fiber writes above hit distinct banks)
+    // coalesced copy of the finished instances to Y
     S* Y = static_cast<S*>(a.Y);
     const unsigned inv = a.cls[td.x].inv;
-    for (int e = tid; e < cnt * L::NX; e += kVlThreads) {
-        const int q = L::NX == 1 ? e : (int)__umulhi((unsigned)e, inv);
-        const int r = e - q * L::NX;
-        Y[(int64_t)yo[q] + r] = ot[q * OSQ + (N + 1) * (r / N) + r % N];
+    for (int e = tid; e < cnt * NX; e += kVlThreads) {
+        const int q = NX == 1 ? e : (int)__umulhi((unsigned)e, inv);
+        const int r = e - q * NX;
+        Y[(int64_t)yo[q] + r] = ot[q * EXQ + KP * (r / N) + r % N];
     }
 }
 
@@ -213,10 +267,12 @@ __global__ void __launch_bounds__(kVlThreads) varlen_kernel(const __grid_constan
     // Offsets of the instances of three consecutive tiles of this CTA (a ring):
     // X offsets then Y offsets, kVlThreads each (a tile has at most that many).
     int* ring = reinterpret_cast<int*>(smem);
-    S* xb0 = reinterpret_cast<S*>(smem + 6 * kVlThreads * sizeof(int));
-    S* xb1 = xb0 + xbuf_elems;
+    // One operand buffer: it is dead after the first contraction, so the last
+    // contraction stages the outputs in it, and the next tile (held in registers
+    // meanwhile) is committed into it after the copy-out.
+    S* xb = reinterpret_cast<S*>(smem + 6 * kVlThreads * sizeof(int));
     float* ex1 = reinterpret_cast<float*>(
-        smem + round_up(6 * kVlThreads * sizeof(int) + 2 * (size_t)xbuf_elems * sizeof(S), 128));
+        smem + round_up(6 * kVlThreads * sizeof(int) + (size_t)xbuf_elems * sizeof(S), 128));
     const int G = gridDim.x;
     const int tid = threadIdx.x;
     const int t0 = blockIdx.x;
@@ -239,12 +295,10 @@ __global__ void __launch_bounds__(kVlThreads) varlen_kernel(const __grid_constan
     __syncthreads();
     S v[kVlRegs];
     vl_prefetch<S>(a, d0, ring, v);
-    vl_commit<S>(d0, v, xb0);
+    vl_commit<S>(d0, v, xb);
     __syncthreads();
     int it = 0;
     for (int tile = t0; tile < a.ntiles; ++it, tile += G) {
-        S* xt = (it & 1) ? xb1 : xb0;
-        S* xn = (it & 1) ? xb0 : xb1;
         const int s0 = it % 3, s1 = (it + 1) % 3, s2 = (it + 2) % 3;
         // offsets of tile + 2G, stored at the end of this tile
         int xo2 = 0, yo2 = 0;
@@ -258,15 +312,14 @@ __global__ void __launch_bounds__(kVlThreads) varlen_kernel(const __grid_constan
         const int P = a.cls[key].P;
         const int n = (key & 15) + 1;
         // exchange buffer 2 starts after P * (per-instance size of buffer 1)
-        float* ex2 = ex1 + (size_t)P * (key < 16 ? stride_mod32(n * n + n - 1, n) : stride_mod32(n * n, n) * n);
+        float* ex2 = ex1 + (size_t)P * vl_kp(n) * (key < 16 ? n : n * n);
         const int* yo = ring + 2 * kVlThreads * s0 + kVlThreads;
-        // the last contraction stages its outputs in the other operand buffer
         if (key < 16)
-            vl_dispatch_n<S, 2>(a, d0, xt, xn, ex1, ex2, yo);
+            vl_dispatch_n<S, 2>(a, d0, xb, xb, ex1, ex2, yo);
         else
-            vl_dispatch_n<S, 3>(a, d0, xt, xn, ex1, ex2, yo);
-        __syncthreads();   // outputs copied out before the next tile lands in xn
-        if (d1.z) vl_commit<S>(d1, v, xn);
+            vl_dispatch_n<S, 3>(a, d0, xb, xb, ex1, ex2, yo);
+        __syncthreads();   // outputs copied out before the next tile lands in xb
+        if (d1.z) vl_commit<S>(d1, v, xb);
         if (tid < d2.z) {
             ring[2 * kVlThreads * s2 + tid] = xo2;
             ring[2 * kVlThreads * s2 + kVlThreads + tid] = yo2;
@@ -282,10 +335,8 @@ __global__ void __launch_bounds__(kVlThreads) varlen_kernel(const __grid_constan
 // Host side
 // ---------------------------------------------------------------------------
 static size_t vl_ex_floats(int kind, int n, int P) {
-    const int su = stride_mod32(n * n + n - 1, n);
-    if (kind == 2) return (size_t)P * su;
-    const int st = stride_mod32(n * n, n);
-    return (size_t)P * ((size_t)st * n + (size_t)su * n);
+    const size_t exq = (size_t)vl_kp(n) * (kind == 2 ? n : n * n);
+    return (size_t)P * exq * (kind == 2 ? 1 : 2);
 }
 
 static int vl_default_P(int kind, int n) {
@@ -364,14 +415,14 @@ static kron_status vl_build(kron_varlen_plan* p) {
             const int c = (int)std::min<int64_t>(P, cnt - s);
             tl.push_back(T{flops * c, make_int4(key, (int)(start + s), c, 0)});
         }
-        max_x = std::max(max_x, (size_t)P * (nx / n) * (n + 1));   // padded output staging
+        max_x = std::max(max_x, (size_t)P * std::max(nx, (nx / n) * vl_kp(n)));   // operands / padded outputs
         max_smem_rest = std::max(max_smem_rest, vl_ex_floats(kind, n, P) * sizeof(float));
     }
     if (p->order.size() > (size_t)INT32_MAX) return KRON_ERR_NOT_SUPPORTED;
     std::stable_sort(tl.begin(), tl.end(), [](const T& a, const T& b) { return a.work > b.work; });
     for (const T& t : tl) p->tiles.push_back(t.td);
     p->xbuf_elems = (int)round_up(max_x, 64);
-    p->smem = round_up(6 * kVlThreads * sizeof(int) + 2 * (size_t)p->xbuf_elems * es, 128) + max_smem_rest;
+    p->smem = round_up(6 * kVlThreads * sizeof(int) + (size_t)p->xbuf_elems * es, 128) + max_smem_rest;
     // Sized for one tile per instance (the most any tile size can give), so that
     // re-tuning never outgrows a workspace sized before it.
     p->ws_bytes = round_up(p->order.size() * sizeof(int4), 256) + 2 * round_up(p->order.size() * 8, 256);
@@ -519,16 +570,15 @@ KRON_API kron_status kron_varlen_plan_create(kron_varlen_plan** plan, int num_cl
         p->present[key] = 1;
         key_of_class[c] = key;
         const int n = d.n, nn = n * n;
+        const int rows = vl_rows(n);
         float* slot = p->args->coef + vl_slot(d.kind, n);
-        const float* A = static_cast<const float*>(d.A);
-        const float* B = static_cast<const float*>(d.B);
-        if (d.kind == 2) {   // Y = B X A^T: mode 1 <- B, mode 2 <- A
-            memcpy(slot, B, nn * sizeof(float));
-            memcpy(slot + nn, A, nn * sizeof(float));
-        } else {             // C on mode 1, B on mode 2, A on mode 3
-            memcpy(slot, d.C, nn * sizeof(float));
-            memcpy(slot + nn, B, nn * sizeof(float));
-            memcpy(slot + 2 * nn, A, nn * sizeof(float));
+        // mode 1 first: 2-D (Y = B X A^T) B, A; 3-D C, B, A
+        const void* mats[3] = {d.kind == 2 ? d.B : d.C, d.kind == 2 ? d.A : d.B, d.A};
+        for (int c = 0; c < d.kind; ++c) {
+            const float* M = static_cast<const float*>(mats[c]);
+            float* dst = slot + c * rows * n;
+            for (int col = 0; col < n; ++col)
+                for (int r = 0; r < rows; ++r) dst[r + rows * col] = r < n ? M[r + n * col] : 0.0f;
         }
         int tp = 0, td = 0;
         kron_get_tile_config(d.kind, n, io, (kron_compute)kVarlenTag, &tp, &td);
