@@ -279,7 +279,7 @@ def cpu_baseline(b, seconds=8.0):
     oracle.build()
     n, inst = b.n, b.n ** b.kind
     f = flops_per_instance(b.kind, n)
-    chunk = max(64, int(2e8 // f))
+    chunk = min(b.batch, max(64, int(2e8 // f)))
     done, t_used = 0, 0.0
     out = np.empty(chunk * inst, np.float32)
     while t_used < seconds and done + chunk <= b.batch:
@@ -562,7 +562,7 @@ def run_reference(args):
     n, inst = b.n, b.n ** b.kind
     f = flops_per_instance(b.kind, n)
     # a bounded sample per step, sized so that warm-up + timed steps take about a minute
-    probe = max(16, int(2e8 // f))
+    probe = min(b.batch, max(16, int(2e8 // f)))
     t = time.perf_counter()
     pout = np.empty(probe * inst, np.float32)
     if b.kind == 2:
@@ -571,7 +571,7 @@ def run_reference(args):
         oracle.kron3(b.A, b.B, b.C, b.X[:probe * inst], ma=n, na=n, mb=n, nb=n, mc=n, nc=n, batch=probe,
                      precision="f32", Y=pout)
     rate = probe / max(1e-6, time.perf_counter() - t)          # instances per second
-    per_step = int(max(16, min(b.batch // 2, rate * 60.0 / (args.steps + args.warmup))))
+    per_step = int(max(1, min(b.batch // 2 or 1, rate * 60.0 / (args.steps + args.warmup))))
     out = np.empty(per_step * inst, np.float32)
 
     def step(i):
