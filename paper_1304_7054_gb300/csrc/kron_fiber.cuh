@@ -354,7 +354,7 @@ kron_status launch_fiber_n(const KronDesc& d, cudaStream_t st) {
         int mult = 1;
         while ((mult * ib) % 16) ++mult;
         P = (P0 + mult - 1) / mult * mult;
-        nstage = d.nstage >= 1 ? d.nstage : 3;
+        nstage = d.nstage >= 1 ? d.nstage : 1;   // more resident CTAs beat a deeper pipeline (measured)
         if (nstage > 8) nstage = 8;
     }
     size_t smem = fiber_smem_bytes<T, S, N, D>(P, nstage);
