@@ -3,7 +3,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
 #include <mutex>
+#include <utility>
 
 #include "kron_device.cuh"
 #include "kron_internal.h"
@@ -45,6 +47,19 @@ const DeviceInfo& device_info() {
         d.device = dev;
     }
     return d;
+}
+
+bool ensure_smem_optin(const void* fn, size_t bytes) {
+    static std::map<std::pair<const void*, int>, size_t> done;
+    static std::mutex mu;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    std::lock_guard<std::mutex> lock(mu);
+    size_t& cur = done[std::make_pair(fn, dev)];
+    if (bytes <= cur) return true;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess) return false;
+    cur = bytes;
+    return true;
 }
 
 unsigned* device_error_word() {

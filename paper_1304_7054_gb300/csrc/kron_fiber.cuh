@@ -78,16 +78,43 @@ __device__ __forceinline__ void contract(const T* __restrict__ M, const T (&x)[N
     }
 }
 
+// Byte span of tile `tile` of a contiguous batch.  The bulk copy takes the
+// 16-byte-aligned superset [a0, a1) of the tile's bytes [b0, b1), clipped to the
+// last whole 16-byte unit of X; the tile's first element then sits `pre` bytes
+// into the shared buffer, and the bytes [h0, b1) past the clip (end of the
+// batch only) are copied by hand.
+struct TileSpan {
+    unsigned pre;     // b0 - a0
+    unsigned copy;    // bytes moved by the bulk copy (multiple of 16)
+    unsigned h0;      // first hand-copied byte, relative to a0
+    unsigned end;     // b1 - a0
+};
+
+template <typename T, typename S, int N, int D>
+__device__ __forceinline__ TileSpan tile_span(const FiberArgs<T, N, D>& a, int64_t tile) {
+    constexpr int64_t NXB = (int64_t)ipow(N, D) * sizeof(S);
+    const int64_t inst0 = tile * a.P;
+    const int64_t cnt = min((int64_t)a.P, a.batch - inst0);
+    const int64_t b0 = inst0 * NXB, b1 = b0 + cnt * NXB;
+    const int64_t a0 = b0 & ~(int64_t)15;
+    const int64_t lim = (a.batch * NXB) & ~(int64_t)15;
+    const int64_t a1 = max(a0, min((b1 + 15) & ~(int64_t)15, lim));
+    TileSpan sp;
+    sp.pre = (unsigned)(b0 - a0);
+    sp.copy = (unsigned)(a1 - a0);
+    sp.h0 = (unsigned)max(a1 - a0, b0 - a0);
+    sp.end = (unsigned)(b1 - a0);
+    return sp;
+}
+
 template <typename T, typename S, int N, int D>
 __device__ __forceinline__ void issue_tile(const FiberArgs<T, N, D>& a, void* dst, uint64_t* bar,
                                            int64_t tile, uint64_t pol) {
-    constexpr int NX = ipow(N, D);
-    const int64_t inst0 = tile * a.P;
-    const int cnt = (int)min((int64_t)a.P, a.batch - inst0);
-    const unsigned bytes = (unsigned)cnt * NX * (unsigned)sizeof(S);
-    const unsigned b16 = bytes & ~15u;
-    mbar_arrive_expect_tx(bar, b16);
-    if (b16) bulk_g2s(dst, static_cast<const S*>(a.X) + inst0 * a.ldxp, b16, bar, pol);
+    constexpr int64_t NXB = (int64_t)ipow(N, D) * sizeof(S);
+    const TileSpan sp = tile_span<T, S, N, D>(a, tile);
+    const char* src = static_cast<const char*>(a.X) + ((tile * a.P * NXB) & ~(int64_t)15);
+    mbar_arrive_expect_tx(bar, sp.copy);
+    if (sp.copy) bulk_g2s(dst, src, sp.copy, bar, pol);
 }
 
 // Strided / transposed / rectangular operand tile, element by element.
@@ -162,7 +189,7 @@ fiber_kernel(const __grid_constant__ FiberArgs<T, N, D> a) {
     const int P = a.P;
     const bool tma = a.nstage > 0;
     const int nbuf = tma ? a.nstage : 1;
-    const size_t xstage = round_up((size_t)P * L::NX * sizeof(S), 128);
+    const size_t xstage = round_up((size_t)P * L::NX * sizeof(S) + 16, 128);
     unsigned char* xbase = smem + 128;
     T* ex1 = reinterpret_cast<T*>(xbase + nbuf * xstage);
     T* ex2 = ex1 + (size_t)P * L::EX1;
@@ -190,17 +217,20 @@ fiber_kernel(const __grid_constant__ FiberArgs<T, N, D> a) {
     int it = 0;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += grid, ++it) {
         const int s = tma ? it % a.nstage : 0;
-        S* xt = reinterpret_cast<S*>(xbase + s * xstage);
+        unsigned char* xraw = xbase + s * xstage;
+        S* xt = reinterpret_cast<S*>(xraw);
         const int64_t inst0 = tile * P;
         const int cnt = (int)min((int64_t)P, a.batch - inst0);
         bool ok = true;
         if (tma) {
             ok = mbar_wait_bounded(&bars[s], (unsigned)(it / a.nstage) & 1u, a.err);
-            const unsigned bytes = (unsigned)cnt * L::NX * (unsigned)sizeof(S);
-            const unsigned b16 = bytes & ~15u;
-            if (bytes != b16) {   // ragged end of the batch: copy the last bytes by hand
-                const S* src = static_cast<const S*>(a.X) + inst0 * a.ldxp;
-                for (int e = b16 / sizeof(S) + tid; e < cnt * L::NX; e += nthr) xt[e] = src[e];
+            const TileSpan sp = tile_span<T, S, N, D>(a, tile);
+            xt = reinterpret_cast<S*>(xraw + sp.pre);
+            if (sp.h0 < sp.end) {   // ragged end of the batch: the last bytes by hand
+                const int64_t a0 = (inst0 * (int64_t)L::NX * (int64_t)sizeof(S)) & ~(int64_t)15;
+                const S* src = reinterpret_cast<const S*>(static_cast<const char*>(a.X) + a0);
+                S* dst = reinterpret_cast<S*>(xraw);
+                for (unsigned e = sp.h0 / sizeof(S) + tid; e < sp.end / sizeof(S); e += nthr) dst[e] = src[e];
                 __syncthreads();
             }
         } else {
@@ -250,7 +280,7 @@ fiber_kernel(const __grid_constant__ FiberArgs<T, N, D> a) {
             const int64_t next = tile + a.nstage * grid;
             if (next < ntiles) {
                 fence_proxy_async_smem();
-                issue_tile<T, S, N, D>(a, xt, &bars[s], next, pol);
+                issue_tile<T, S, N, D>(a, xraw, &bars[s], next, pol);
             }
         }
 
@@ -307,7 +337,7 @@ template <typename T, typename S, int N, int D>
 size_t fiber_smem_bytes(int P, int nstage) {
     using L = FiberLayout<N, D>;
     const int nbuf = nstage > 0 ? nstage : 1;
-    return 128 + nbuf * round_up((size_t)P * L::NX * sizeof(S), 128) +
+    return 128 + nbuf * round_up((size_t)P * L::NX * sizeof(S) + 16, 128) +
            (size_t)P * (L::EX1 + L::EX2) * sizeof(T);
 }
 
@@ -343,17 +373,13 @@ kron_status launch_fiber_n(const KronDesc& d, cudaStream_t st) {
     a.err = device_error_word();
     if (!a.err) return KRON_ERR_CUDA;
 
-    // Instances per tile: about one fiber per thread and stage; bulk-copied tiles
-    // must be a multiple of 16 bytes.  If that rounding makes the tile too large
-    // for shared memory, the tile is loaded element by element instead.
+    // Instances per tile: about one fiber per thread and stage (tiles of any size
+    // can be bulk-copied, see tile_span).  If the tile does not fit in shared
+    // memory with a bulk-copy buffer, it is loaded element by element instead.
     const int P0 = d.P > 0 ? d.P : (kFiberThreads + L::FPI - 1) / L::FPI;
     int P = P0;
     int nstage = 0;
     if (d.contiguous) {
-        const size_t ib = L::NX * sizeof(S);
-        int mult = 1;
-        while ((mult * ib) % 16) ++mult;
-        P = (P0 + mult - 1) / mult * mult;
         nstage = d.nstage >= 1 ? d.nstage : 1;   // more resident CTAs beat a deeper pipeline (measured)
         if (nstage > 8) nstage = 8;
     }
@@ -373,12 +399,7 @@ kron_status launch_fiber_n(const KronDesc& d, cudaStream_t st) {
     a.nstage = nstage;
 
     auto kern = fiber_kernel<T, S, N, D>;
-    static int smem_set = 0;   // largest opt-in already applied to this instantiation
-    if ((int)smem > smem_set) {
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-            return KRON_ERR_CUDA;
-        smem_set = (int)smem;
-    }
+    if (!ensure_smem_optin((const void*)kern, smem)) return KRON_ERR_CUDA;
     const int64_t ntiles = (d.batch + P - 1) / P;
     int64_t grid = d.grid;
     if (grid <= 0) {

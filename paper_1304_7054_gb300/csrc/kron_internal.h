@@ -88,4 +88,8 @@ struct DeviceInfo {
 };
 const DeviceInfo& device_info();
 
+// Raises the dynamic shared-memory limit of kernel `fn` on the current device to
+// at least `bytes` (remembered per kernel and device).  False on a CUDA error.
+bool ensure_smem_optin(const void* fn, size_t bytes);
+
 }  // namespace kron

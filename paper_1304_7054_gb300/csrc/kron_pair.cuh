@@ -456,12 +456,7 @@ kron_status launch_pair_n(const KronDesc& d, cudaStream_t st) {
     a.P = P;
     a.nstage = nstage;
     auto kern = pair_kernel<S, N, D, NT>;
-    static int smem_set = 0;
-    if ((int)smem > smem_set) {
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-            return KRON_ERR_CUDA;
-        smem_set = (int)smem;
-    }
+    if (!ensure_smem_optin((const void*)kern, smem)) return KRON_ERR_CUDA;
     const int64_t ntiles = (d.batch + P - 1) / P;
     int64_t grid = d.grid;
     if (grid <= 0) {

@@ -531,12 +531,7 @@ static kron_status launch_tc2_n(const KronDesc& d, cudaStream_t st) {
     a.P = P;
     a.nstage = nstage;
     auto kern = tc2_kernel<S, N>;
-    static int smem_set = 0;
-    if ((int)smem > smem_set) {
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-            return KRON_ERR_CUDA;
-        smem_set = (int)smem;
-    }
+    if (!ensure_smem_optin((const void*)kern, smem)) return KRON_ERR_CUDA;
     const int64_t ntiles = (d.batch + P - 1) / P;
     int64_t grid = d.grid;
     if (grid <= 0) {
@@ -571,12 +566,7 @@ static kron_status launch_tc3_n(const KronDesc& d, cudaStream_t st) {
     const size_t smem = 128 + kTc3Warps * (size_t)Tc3Layout<N>::PER_WARP;
     if (smem > dev.smem_per_block_optin) return KRON_ERR_NOT_SUPPORTED;
     auto kern = tc3_kernel<N>;
-    static int smem_set = 0;
-    if ((int)smem > smem_set) {
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-            return KRON_ERR_CUDA;
-        smem_set = (int)smem;
-    }
+    if (!ensure_smem_optin((const void*)kern, smem)) return KRON_ERR_CUDA;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * kTc3Warps, smem) != cudaSuccess)
         return KRON_ERR_CUDA;

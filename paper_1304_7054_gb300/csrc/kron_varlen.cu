@@ -363,7 +363,6 @@ struct kron_varlen_plan {
     std::vector<int4> tiles;
     size_t ws_bytes = 0;
     size_t smem = 0;
-    size_t smem_set = 0;                       // opt-in last applied by this plan
     int xbuf_elems = 0;
     int grid = 0;
     kron::VarlenArgs* args = nullptr;          // heap: ~30 KB
@@ -481,11 +480,7 @@ static kron_status vl_launch(kron_varlen_plan* p, const void* X, void* Y, void* 
     if (dev.sms <= 0) return KRON_ERR_CUDA;
     if (p->smem > dev.smem_per_block_optin) return KRON_ERR_NOT_SUPPORTED;
     void* fn = vl_kernel_ptr(p->io);
-    if (p->smem_set != p->smem) {
-        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem) != cudaSuccess)
-            return KRON_ERR_CUDA;
-        p->smem_set = p->smem;
-    }
+    if (!ensure_smem_optin(fn, p->smem)) return KRON_ERR_CUDA;
     if (p->uploaded_ws != ws || p->uploaded_version != p->version) {
         kron_status r = vl_upload(p, ws, st);
         if (r != KRON_OK) return r;
