@@ -514,15 +514,14 @@ static kron_status launch_tc2_n(const KronDesc& d, cudaStream_t st) {
     a.alpha_one = d.alpha == 1.0;
     a.err = device_error_word();
     if (!a.err) return KRON_ERR_CUDA;
-    // Defaults measured at n = 16: 32 KB operand tiles, three stages for FP32
-    // storage (32 instances), two for bf16 (64 instances); smaller n keep the
-    // tile size in bytes.
-    constexpr int P16 = sizeof(S) == 4 ? 32 : 64;
-    int P = d.P > 0 ? d.P : std::min(1024, P16 * 256 / (N * N));
+    // Measured defaults: at n = 16, 32 KB operand tiles (32 FP32 or 64 bf16
+    // instances; three / two stages); below 16 instances of fewer bytes, 16 per tile
+    // and three stages (more resident CTAs).
+    int P = d.P > 0 ? d.P : (N == 16 ? (sizeof(S) == 4 ? 32 : 64) : 16);
     int mult = 1;
     while ((mult * N * N * sizeof(S)) % 16) ++mult;
     P = (P + mult - 1) / mult * mult;
-    int nstage = d.nstage >= 1 ? d.nstage : (sizeof(S) == 4 ? 3 : 2);
+    int nstage = d.nstage >= 1 ? d.nstage : ((N == 16 && sizeof(S) == 2) ? 2 : 3);
     if (nstage > 8) nstage = 8;
     auto smem_of = [&](int ns) { return 128 + ns * round_up((size_t)P * N * N * sizeof(S), 128); };
     size_t smem = smem_of(nstage);
