@@ -317,7 +317,7 @@ def cpu_baseline(b, seconds=8.0):
                       f"{t_used:.1f} s"}
 
 
-def measure_variant(kg, name, steps, warmup, torch, dev, peaks):
+def measure_variant(kg, name, steps, warmup, torch, dev, peaks, tune=True):
     wl = WORKLOADS[name]
     b = make_inputs(wl)
     try:
@@ -326,6 +326,9 @@ def measure_variant(kg, name, steps, warmup, torch, dev, peaks):
         call(kg, b, X, Y, wl["compute"])
     except kg.KronError as e:
         return {"unavailable": str(e)}
+    tile = None
+    if tune:   # the library's autotuner picks the tile size and pipeline depth (untimed)
+        tile = kg.autotune(b.kind, b.n, b.batch, X, Y, compute=wl["compute"])
     total_ms, kern_ms = time_device(kg, b, X, Y, wl["compute"], steps, warmup, torch)
     err = sample_error(kg, b, Y, wl["io"], torch)
     fl = flops_per_instance(b.kind, b.n) * b.batch
@@ -333,7 +336,8 @@ def measure_variant(kg, name, steps, warmup, torch, dev, peaks):
     gbs = by / (kern_ms * 1e-3) / 1e9
     r = {"gflops": round(fl / (kern_ms * 1e-3) / 1e9, 1), "hbm_gbs": round(gbs, 1),
          "hbm_frac": round(gbs / peaks["hbm"], 4), "ms": round(kern_ms, 4), "batch": b.batch,
-         "kernel": kernel_of(b.kind, b.n, wl["io"], wl["compute"]), "max_norm_err_vs_fp64_oracle": err}
+         "kernel": kernel_of(b.kind, b.n, wl["io"], wl["compute"]), "max_norm_err_vs_fp64_oracle": err,
+         "tile": {"instances": tile[0], "pipeline_depth": tile[1]} if tile else None}
     del X, Y
     torch.cuda.empty_cache()
     return r

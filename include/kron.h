@@ -151,9 +151,11 @@ KRON_API kron_status kron_device_status(kron_stream_t stream);
  * instances processed per CTA tile and depth of the bulk-copy pipeline (both 0
  * = built-in default).  kron_autotune times the candidate configurations on the
  * caller's buffers (contiguous X and Y of batch_count instances, minimal
- * leading dimensions; Y is overwritten), keeps the fastest in the process-wide
- * table, appends it to the file named by KRON_TUNE_CACHE (if set; read at first
- * use), and returns it.  Errors: KRON_ERR_INVALID_VALUE for bad arguments,
+ * leading dimensions; Y is overwritten; each candidate is timed as the best of
+ * three rounds of ten launches), keeps the fastest in the process-wide table
+ * unless it beats the built-in default by less than 2% (then the default, 0 0,
+ * is kept), appends the choice to the file named by KRON_TUNE_CACHE (if set;
+ * read at first use; later lines override earlier ones), and returns it.  Errors: KRON_ERR_INVALID_VALUE for bad arguments,
  * KRON_ERR_CUDA if a timing call fails.
  */
 KRON_API kron_status kron_set_tile_config(int kind, int n, kron_dtype io, kron_compute comp,

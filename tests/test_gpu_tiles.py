@@ -34,7 +34,8 @@ def test_autotune_then_correct(kind, n):
     X = torch.from_numpy(b.X).cuda()
     scratch = torch.empty_like(X)
     P, depth = kg.autotune(kind, n, b.batch, X, scratch)
-    assert P >= 1 and depth >= 1
+    # (0, 0) means no candidate beat the built-in default clearly enough.
+    assert (P, depth) == (0, 0) or (P >= 1 and depth >= 1)
     assert kg.get_tile_config(kind, n, "f32") == (P, depth)
     try:
         Y, X64 = run_gpu(b)
