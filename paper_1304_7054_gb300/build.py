@@ -72,13 +72,16 @@ if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
 
 
-# Sources that define each kernel family (its device code, launcher and dispatch).
+# Sources that define each kernel family: its device code and its launcher (tile
+# size, pipeline depth, grid).  Argument checking and dispatch are left out: they
+# decide which kernel runs, not what a launch of it does.
 FAMILY_SOURCES = {
-    "pair_kernel": ["kron_pair.cuh", "kron_fiber.cuh", "kron_device.cuh", "kron_internal.h", "kron_api.cu"],
-    "fiber_kernel": ["kron_fiber.cuh", "kron_device.cuh", "kron_internal.h", "kron_api.cu"],
-    "tc2_kernel": ["kron_tc.cu", "kron_fiber.cuh", "kron_device.cuh", "kron_internal.h", "kron_api.cu"],
-    "tc3_kernel": ["kron_tc.cu", "kron_fiber.cuh", "kron_device.cuh", "kron_internal.h", "kron_api.cu"],
-    "varlen_kernel": ["kron_varlen.cu", "kron_fiber.cuh", "kron_device.cuh", "kron_internal.h"],
+    "pair_kernel": ["kron_pair.cuh", "kron_fiber.cuh", "kron_device.cuh"],
+    "pair16_kernel": ["kron_pair16.cu", "kron_pair.cuh", "kron_fiber.cuh", "kron_device.cuh"],
+    "fiber_kernel": ["kron_fiber.cuh", "kron_device.cuh"],
+    "tc2_kernel": ["kron_tc.cu", "kron_fiber.cuh", "kron_device.cuh"],
+    "tc3_kernel": ["kron_tc.cu", "kron_fiber.cuh", "kron_device.cuh"],
+    "varlen_kernel": ["kron_varlen.cu", "kron_fiber.cuh", "kron_device.cuh"],
 }
 
 

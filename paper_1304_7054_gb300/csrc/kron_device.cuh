@@ -53,26 +53,33 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned by
                  : "memory");
 }
 
+// Longest time one try_wait may keep the thread suspended; it resumes as soon as
+// the phase completes.  Without the hint the wait returns after a short
+// system-defined time, and the retries cost issue slots and shared-memory
+// bandwidth that the compute warps of the same SM need.
+constexpr unsigned kWaitSuspendNs = 1000000u;
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
     unsigned ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(kWaitSuspendNs)
         : "memory");
     return ok != 0;
 }
 
-// Waits for phase `parity` of `bar` to complete, for at most kWaitLimitNs.
-// On expiry it records kDevErrTimeout in *err and returns false.
+// Waits for phase `parity` of `bar` to complete, for at most kWaitLimitNs (plus
+// at most 8 suspensions of kWaitSuspendNs).  On expiry it records
+// kDevErrTimeout in *err and returns false.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, unsigned* err) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_timer_ns();
     for (;;) {
 #pragma unroll 1
-        for (int i = 0; i < 32; ++i)
+        for (int i = 0; i < 8; ++i)
             if (mbar_try_wait(bar, parity)) return true;
         if (global_timer_ns() - t0 > kWaitLimitNs) {
             atomicOr(err, kDevErrTimeout);

@@ -1,0 +1,278 @@
+// 2-D FP32 pair kernel for n = 16 with the mode exchange done in place.
+//
+// The two contractions are those of the generic pair kernel (Sec. 2.1, the
+// 2-D case of Algorithm 1: mode 2 with M2 = op(A) as pairs of fibers, then
+// mode 1 with M1 = op(B) as pairs of rows), specialised to the paper's largest
+// size in single precision:
+//
+//  * The intermediate W = X M2^T overwrites the operand tile: a thread reads
+//    rows (l, l+1) of one instance into registers and writes rows (l, l+1) of
+//    W to the same 32 words, and the second stage reads column j of W, whose
+//    16 words no other thread touches.  The tile buffer is then the only
+//    on-chip storage of a tile: 18 KB per tile, where the generic layout needs
+//    54 KB for one tile and its exchange buffers.
+//  * Instance q of a tile sits at word 288 q + r(q), with r(q) = 16 (q & 1) +
+//    4 ((q >> 1) & 3).  The first stage (two instances per half-warp, 8-byte
+//    accesses) and the second (eight instances per quarter-warp, 16-byte
+//    accesses, one column each) then touch 32 distinct banks per access.
+//  * The results overwrite W in place as well, and leave with one 1 KB bulk
+//    copy (TMA) per instance, so L2 receives whole lines.
+//  * One producer warp streams tiles in and results out through a ring of
+//    buffers (full / empty mbarriers), one 1 KB bulk copy per instance each
+//    way; the four compute warps never issue a global memory access (except
+//    the reads of Y that beta != 0 needs).
+#include "kron_pair.cuh"
+
+namespace kron {
+
+namespace {
+
+constexpr int kN = 16, kNX = 256;
+constexpr int kTileP = 16;                  // instances per tile
+constexpr int kSlot = 288;                  // words between instance slots
+constexpr int kTileWords = kTileP * kSlot;  // 18 KB per buffer
+constexpr int kCompute = 128;               // compute threads (4 warps)
+constexpr int kThreads = kCompute + 32;     // + one producer warp
+constexpr int kMaxRing = 4;
+
+__device__ __forceinline__ int slot_of(int q) { return kSlot * q + 16 * (q & 1) + 4 * ((q >> 1) & 3); }
+
+// Barrier 1 over the 128 compute threads; returns the OR of v over them.
+__device__ __forceinline__ bool compute_sync_or(bool v) {
+    unsigned r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "bar.red.or.pred p, 1, 128, q;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(r)
+        : "r"((unsigned)v)
+        : "memory");
+    return r != 0;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// 1-D bulk copy (TMA) shared -> global in the thread's current bulk group.
+// dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void bulk_s2g(void* dst, const void* src, unsigned bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// The shared-memory sources of this thread's bulk stores have been read.
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// This thread's bulk stores are complete.
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+__device__ __forceinline__ void load_col(const float* p, float (&w)[kN]) {
+#pragma unroll
+    for (int c = 0; c < kN / 4; ++c) {
+        const float4 v = *reinterpret_cast<const float4*>(p + 4 * c);
+        w[4 * c] = v.x;
+        w[4 * c + 1] = v.y;
+        w[4 * c + 2] = v.z;
+        w[4 * c + 3] = v.w;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 6) pair16_kernel(const __grid_constant__ PairArgs<kN, 2> a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem);
+    uint64_t* empty = full + kMaxRing;
+    float* ring = reinterpret_cast<float*>(smem + 128);
+    const int NB = a.nstage;
+    const int tid = threadIdx.x;
+    const int64_t ntiles = (a.batch + kTileP - 1) / kTileP;
+    const int64_t grid = gridDim.x;
+
+    if (tid == 0) {
+        for (int s = 0; s < NB; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kCompute);
+        }
+        fence_barrier_init();
+    }
+    __syncthreads();
+
+    if (tid >= kCompute) {
+        // Producer: tile `it` goes to buffer it % NB once the compute threads have
+        // released that buffer's previous tile (it - NB), whose results they left
+        // in the buffer: those are stored first, with one bulk copy per instance.
+        const int lane = tid - kCompute;
+        const uint64_t pol = l2_evict_first_policy();
+        float* Y = static_cast<float*>(a.Y);
+        auto store_tile = [&](int s, int64_t t) {
+            const int64_t i0 = t * kTileP;
+            const int c = (int)min((int64_t)kTileP, a.batch - i0);
+            if (lane < c) {
+                bulk_s2g(Y + (i0 + lane) * kNX, ring + s * kTileWords + slot_of(lane), kNX * 4u);
+                bulk_commit();
+            }
+        };
+        int it = 0;
+        for (int64_t tile = blockIdx.x; tile < ntiles; tile += grid, ++it) {
+            const int s = it % NB;
+            if (it >= NB) {
+                if (!mbar_wait_bounded(&empty[s], (unsigned)(it / NB - 1) & 1u, a.err)) {
+                    bulk_wait_all();
+                    return;
+                }
+                store_tile(s, tile - (int64_t)NB * grid);
+                bulk_wait_read();   // the results have left the buffer
+            }
+            const int64_t inst0 = tile * kTileP;
+            const int cnt = (int)min((int64_t)kTileP, a.batch - inst0);
+            float* buf = ring + s * kTileWords;
+            // The compute threads' generic accesses to this buffer happen before their
+            // arrival on empty[s]; order them before the bulk copies that overwrite it.
+            fence_proxy_async_smem();
+            if (lane == 0) mbar_arrive_expect_tx(&full[s], (unsigned)cnt * kNX * 4u);
+            __syncwarp();
+            if (lane < cnt)
+                bulk_g2s(buf + slot_of(lane), static_cast<const float*>(a.X) + (inst0 + lane) * kNX, kNX * 4u,
+                         &full[s], pol);
+        }
+        for (int j = it > NB ? it - NB : 0; j < it; ++j) {   // the last tiles' results
+            if (!mbar_wait_bounded(&empty[j % NB], (unsigned)(j / NB) & 1u, a.err)) break;
+            store_tile(j % NB, blockIdx.x + (int64_t)j * grid);
+        }
+        bulk_wait_all();
+        return;
+    }
+
+    const f2* m1p = reinterpret_cast<const f2*>(a.m1);
+    const float* Y = static_cast<const float*>(a.Y);
+    int it = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += grid, ++it) {
+        const int s = it % NB;
+        float* buf = ring + s * kTileWords;
+        const int64_t inst0 = tile * kTileP;
+        const int cnt = (int)min((int64_t)kTileP, a.batch - inst0);
+        const bool ok = mbar_wait_bounded(&full[s], (unsigned)(it / NB) & 1u, a.err);
+
+        // Stage 1: rows (l, l+1) of instance q times M2^T, written back in place.
+        {
+            const int q = tid >> 3, l = 2 * (tid & 7);
+            if (q < cnt) {
+                float* p = buf + slot_of(q) + l;
+                f2 x[kN];
+#pragma unroll
+                for (int m = 0; m < kN; ++m) x[m] = *reinterpret_cast<const f2*>(p + kN * m);
+                f2 w[kN];
+                contract_dup<kN>(a.da, x, w);
+#pragma unroll
+                for (int j = 0; j < kN; ++j) *reinterpret_cast<f2*>(p + kN * j) = w[j];
+            }
+        }
+        if (compute_sync_or(!ok)) {
+            // A copy did not land in time: wait (bounded) for the ones that may still
+            // be in flight into this CTA's buffers, then give up.  The producer cannot
+            // issue beyond tile it + NB - 1, whose buffer this iteration still holds.
+            if (tid == 0)
+                for (int j = it; j < it + NB; ++j)
+                    if (blockIdx.x + (int64_t)j * grid < ntiles)
+                        mbar_wait_bounded(&full[j % NB], (unsigned)(j / NB) & 1u, a.err);
+            return;
+        }
+
+        // Stage 2: column j of W of instance q times M1 (pairs of output rows); the
+        // results overwrite the column.  Partial 16-byte stores from registers
+        // would reach L2 as half sectors (1.7x the bytes of Y); the producer's
+        // bulk copies write whole lines.
+        const int q = tid & 15, j0 = tid >> 4;
+        const bool live = q < cnt;
+        float* wq = buf + slot_of(q);
+        const float* yq = Y + (inst0 + q) * kNX;
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+            const int j = j0 + 8 * h;
+            if (!live) continue;
+            float w[kN];
+            load_col(wq + kN * j, w);
+            f2 y[kN / 2];
+            contract_rows<kN>(m1p, w, y);
+            if (!a.alpha_one) {
+                const f2 al = f2_pack(a.alpha, a.alpha);
+#pragma unroll
+                for (int r = 0; r < kN / 2; ++r) y[r] = fmul2(y[r], al);
+            }
+            if (!a.beta_zero) {
+                const f2 be = f2_pack(a.beta, a.beta);
+#pragma unroll
+                for (int r = 0; r < kN / 2; ++r) y[r] = ffma2(be, load_pair<float>(yq + kN * j + 2 * r), y[r]);
+            }
+#pragma unroll
+            for (int c = 0; c < kN / 4; ++c)
+                *reinterpret_cast<uint4*>(wq + kN * j + 4 * c) = make_uint4(
+                    (unsigned)y[2 * c], (unsigned)(y[2 * c] >> 32), (unsigned)y[2 * c + 1], (unsigned)(y[2 * c + 1] >> 32));
+        }
+        fence_proxy_async_smem();   // results written: visible to the bulk stores
+        mbar_arrive(&empty[s]);
+    }
+}
+
+size_t pair16_smem_bytes(int nb) { return 128 + (size_t)nb * kTileWords * sizeof(float); }
+
+}  // namespace
+
+// 2-D, n = 16, FP32 storage and arithmetic, contiguous X and Y.  Tile sizes
+// other than 16 instances are left to the generic pair kernel.
+kron_status launch_pair16(const KronDesc& d, cudaStream_t st) {
+    if (d.D != 2 || d.N != kN || d.io != KRON_R32F || d.comp != KRON_COMPUTE_NATIVE || !d.contiguous ||
+        !d.ycontig || (d.P > 0 && d.P != kTileP))
+        return KRON_ERR_NOT_SUPPORTED;
+    const DeviceInfo& dev = device_info();
+    if (dev.sms <= 0) return KRON_ERR_CUDA;
+    PairArgs<kN, 2> a;
+    auto dup = [](double x) {
+        const float v = (float)x;
+        unsigned b;
+        memcpy(&b, &v, sizeof(b));
+        return ((f2)b << 32) | (f2)b;
+    };
+    for (int e = 0; e < kN * kN; ++e) {
+        a.da[e] = dup(d.m2[e]);
+        a.m1[e] = (float)d.m1[e];
+    }
+    a.db[0] = 0;
+    a.X = d.X;
+    a.Y = d.Y;
+    a.batch = d.batch;
+    a.alpha = (float)d.alpha;
+    a.beta = (float)d.beta;
+    a.beta_zero = d.beta == 0.0;
+    a.alpha_one = d.alpha == 1.0;
+    a.err = device_error_word();
+    if (!a.err) return KRON_ERR_CUDA;
+    a.P = kTileP;
+    // One buffer per CTA (measured best: the six to seven resident CTAs per SM
+    // overlap one another's copies; a second buffer costs resident CTAs).
+    int nb = d.nstage >= 1 ? d.nstage : 1;
+    if (nb > kMaxRing) nb = kMaxRing;
+    size_t smem = pair16_smem_bytes(nb);
+    while (nb > 1 && smem > dev.smem_per_block_optin) smem = pair16_smem_bytes(--nb);
+    if (smem > dev.smem_per_block_optin) return KRON_ERR_NOT_SUPPORTED;
+    a.nstage = nb;
+    const void* kern = (const void*)pair16_kernel;
+    if (!ensure_smem_optin(kern, smem)) return KRON_ERR_CUDA;
+    const int64_t ntiles = (d.batch + kTileP - 1) / kTileP;
+    int64_t grid = d.grid;
+    if (grid <= 0) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem) != cudaSuccess)
+            return KRON_ERR_CUDA;
+        grid = (int64_t)(per_sm < 1 ? 1 : per_sm) * dev.sms;
+    }
+    if (grid > ntiles) grid = ntiles;
+    if (grid < 1) grid = 1;
+    void* args[] = {&a};
+    if (cudaLaunchKernel(kern, dim3((unsigned)grid), dim3(kThreads), args, smem, st) != cudaSuccess)
+        return KRON_ERR_CUDA;
+    return cudaPeekAtLastError() == cudaSuccess ? KRON_OK : KRON_ERR_CUDA;
+}
+
+}  // namespace kron

@@ -22,7 +22,9 @@ def test_reference_arm_json_line():
 def test_kernel_names_follow_dispatch():
     sys.path.insert(0, ROOT)
     import bench
-    assert bench.kernel_of(2, 16, "f32", "native").startswith("pair_kernel")
+    assert bench.kernel_of(2, 16, "f32", "native").startswith("pair16_kernel")
+    assert bench.kernel_of(2, 14, "f32", "native").startswith("pair_kernel")
+    assert bench.kernel_of(2, 16, "bf16", "native").startswith("pair_kernel")
     assert bench.kernel_of(3, 15, "f32", "native").startswith("fiber_kernel")
     assert bench.kernel_of(2, 16, "f64", "native").startswith("fiber_kernel")
     assert bench.kernel_of(3, 16, "f32", "bf16x3").startswith("tc3_kernel")
