@@ -118,7 +118,11 @@ static kron_status dispatch(KronDesc& d, cudaStream_t st) {
     apply_tile_config(d);
     if (d.comp == KRON_COMPUTE_32F_BF16X3) return launch_tc(d, st);
     if (d.contiguous && d.ycontig && d.N % 2 == 0 && d.io != KRON_R64F) {
-        kron_status r = d.D == 2 && d.N == 16 && d.io == KRON_R32F ? launch_pair16(d, st) : KRON_ERR_NOT_SUPPORTED;
+        kron_status r = KRON_ERR_NOT_SUPPORTED;
+        if (d.D == 2 && d.io == KRON_R32F) {   // in-place kernels where they beat the generic one
+            if (d.N == 16) r = launch_pair16(d, st);
+            else if (d.N == 10 || d.N == 14) r = launch_pair2ip(d, st);
+        }
         if (r != KRON_ERR_NOT_SUPPORTED) return r;
         switch (d.io) {
             case KRON_R32F: r = d.D == 2 ? launch_pair_f32_d2(d, st) : launch_pair_f32_d3(d, st); break;

@@ -79,6 +79,9 @@ kron_status launch_pair_f16_d3(const KronDesc& d, cudaStream_t s);
 // 2-D n = 16 FP32 pair kernel with the exchange in place in the operand tile
 // (contiguous X and Y, 16 instances per tile); KRON_ERR_NOT_SUPPORTED otherwise.
 kron_status launch_pair16(const KronDesc& d, cudaStream_t s);
+// 2-D n = 10, 14 FP32 pair kernels with the exchange in place (tiles of a
+// multiple of 8 instances); KRON_ERR_NOT_SUPPORTED otherwise.
+kron_status launch_pair2ip(const KronDesc& d, cudaStream_t s);
 
 // Tensor-core split-precision kernels (R32F or R16BF storage).
 kron_status launch_tc(const KronDesc& d, cudaStream_t s);

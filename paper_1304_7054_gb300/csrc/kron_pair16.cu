@@ -37,37 +37,6 @@ constexpr int kMaxRing = 4;
 
 __device__ __forceinline__ int slot_of(int q) { return kSlot * q + 16 * (q & 1) + 4 * ((q >> 1) & 3); }
 
-// Barrier 1 over the 128 compute threads; returns the OR of v over them.
-__device__ __forceinline__ bool compute_sync_or(bool v) {
-    unsigned r;
-    asm volatile(
-        "{\n\t.reg .pred p, q;\n\t"
-        "setp.ne.u32 q, %1, 0;\n\t"
-        "bar.red.or.pred p, 1, 128, q;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(r)
-        : "r"((unsigned)v)
-        : "memory");
-    return r != 0;
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-// 1-D bulk copy (TMA) shared -> global in the thread's current bulk group.
-// dst, src 16-byte aligned; bytes a multiple of 16.
-__device__ __forceinline__ void bulk_s2g(void* dst, const void* src, unsigned bytes) {
-    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
-                 "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-// The shared-memory sources of this thread's bulk stores have been read.
-__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
-// This thread's bulk stores are complete.
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
-
 __device__ __forceinline__ void load_col(const float* p, float (&w)[kN]) {
 #pragma unroll
     for (int c = 0; c < kN / 4; ++c) {

@@ -23,7 +23,8 @@ def test_kernel_names_follow_dispatch():
     sys.path.insert(0, ROOT)
     import bench
     assert bench.kernel_of(2, 16, "f32", "native").startswith("pair16_kernel")
-    assert bench.kernel_of(2, 14, "f32", "native").startswith("pair_kernel")
+    assert bench.kernel_of(2, 10, "f32", "native").startswith("pair2ip_kernel")
+    assert bench.kernel_of(2, 12, "f32", "native").startswith("pair_kernel")
     assert bench.kernel_of(2, 16, "bf16", "native").startswith("pair_kernel")
     assert bench.kernel_of(3, 15, "f32", "native").startswith("fiber_kernel")
     assert bench.kernel_of(2, 16, "f64", "native").startswith("fiber_kernel")
