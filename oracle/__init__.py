@@ -12,6 +12,10 @@ Three independent evaluations of the same operation (paper Sec. 2.1 / 2.2):
 * ``kron_matrix`` + ``matvec`` -- the explicit Kronecker matrix built from the
   block definition of Sec. 2, for tiny sizes.
 
+It also holds the paper's two other interfaces of Sec. 3 as direct sums:
+``kron1`` (TKRON1, the 1-D product, a batched GEMV with a shared matrix) and
+``gemm_a`` (TGEMM_A, a batched GEMM whose first factor varies across the batch).
+
 Conventions: ``kron2(A, B)`` computes ``vec(Y) = (op(A) (x) op(B)) vec(op(X))``,
 i.e. ``Y = op(B) op(X) op(A)^T``; ``kron3(A, B, C)`` applies
 ``op(A) (x) op(B) (x) op(C)`` with C on mode 1, B on mode 2, A on mode 3.
@@ -80,6 +84,13 @@ def bind(lib: ctypes.CDLL) -> ctypes.CDLL:
             fn.argtypes = [_C, _C, _C, _I, _I, _I, _I, _I, _I, _L, scal, _P, _I, _P, _I, _P, _I,
                            _P, _I, _I, _L, scal, _P, _I, _I, _L]
             fn.restype = None
+    for suf, scal in (("f64", _D), ("f32", _F)):
+        fn = getattr(lib, "oracle_kron1_" + suf)
+        fn.argtypes = [_C, _I, _I, _L, scal, _P, _I, _P, _L, scal, _P, _L]
+        fn.restype = None
+        fn = getattr(lib, "oracle_gemm_a_" + suf)
+        fn.argtypes = [_C, _C, _I, _I, _I, scal, _P, _I, _L, _P, _I, scal, _P, _I, _L, _L]
+        fn.restype = None
     lib.oracle_kron_matrix_f64.argtypes = [_I, _I, _I, _I, _P, _I, _P, _I, _P]
     lib.oracle_kron_matrix_f64.restype = None
     lib.oracle_matvec_f64.argtypes = [_L, _L, _P, _P, _P]
@@ -177,6 +188,48 @@ def kron3(A, B, C, X, *, ma, na, mb, nb, mc, nc, batch, lda=None, ldb=None, ldc=
     fn(_b(ta), _b(tb), _b(tc), ma, na, mb, nb, mc, nc, batch, alpha, _ptr(A), lda, _ptr(B), ldb,
        _ptr(C), ldc, _ptr(X), ldx, ldx2, ldxp, beta, _ptr(Y), ldy, ldy2, ldyp)
     return Y
+
+
+def kron1(A, X, *, ma, na, batch, lda=None, ldxp=None, ldyp=None, alpha=1.0, beta=0.0, Y=None,
+          transa="N", precision="f64", lib_override=None):
+    """TKRON1 (Sec. 3): y^p <- alpha op(A) x^p + beta y^p, op(A): ma x na."""
+    dt = _dt(precision)
+    ta = transa.upper()
+    lda = lda or (ma if ta == "N" else na)
+    ldxp = na if ldxp is None else ldxp
+    ldyp = ma if ldyp is None else ldyp
+    A = np.ascontiguousarray(A, dtype=dt).ravel()
+    X = np.ascontiguousarray(X, dtype=dt).ravel()
+    if Y is None:
+        Y = np.zeros(max(1, (batch - 1) * ldyp + ma), dtype=dt)
+    else:
+        Y = np.array(Y, dtype=dt, copy=True).ravel()
+    L = lib_override or lib()
+    getattr(L, f"oracle_kron1_{precision}")(_b(ta), ma, na, batch, alpha, _ptr(A), lda, _ptr(X), ldxp,
+                                            beta, _ptr(Y), ldyp)
+    return Y
+
+
+def gemm_a(A, B, *, m, n, k, batch, lda=None, lda2=None, ldb=None, ldc=None, ldc2=None, alpha=1.0,
+           beta=0.0, C=None, transa="N", transb="N", precision="f64", lib_override=None):
+    """TGEMM_A (Sec. 3): C^p <- alpha op(A^p) op(B) + beta C^p; A varies, B is shared."""
+    dt = _dt(precision)
+    ta, tb = transa.upper(), transb.upper()
+    lda = lda or (m if ta == "N" else k)
+    lda2 = lda * (k if ta == "N" else m) if lda2 is None else lda2
+    ldb = ldb or (k if tb == "N" else n)
+    ldc = ldc or m
+    ldc2 = ldc * n if ldc2 is None else ldc2
+    A = np.ascontiguousarray(A, dtype=dt).ravel()
+    B = np.ascontiguousarray(B, dtype=dt).ravel()
+    if C is None:
+        C = np.zeros(max(1, (batch - 1) * ldc2 + ldc * (n - 1) + m), dtype=dt)
+    else:
+        C = np.array(C, dtype=dt, copy=True).ravel()
+    L = lib_override or lib()
+    getattr(L, f"oracle_gemm_a_{precision}")(_b(ta), _b(tb), m, n, k, alpha, _ptr(A), lda, lda2, _ptr(B),
+                                             ldb, beta, _ptr(C), ldc, ldc2, batch)
+    return C
 
 
 def kron_matrix(A, B, lib_override=None):

@@ -22,6 +22,9 @@
  *
  * beta == 0 means Y is not read (BLAS convention), so NaN in Y is ignored.
  *
+ * The paper's 1-D interface (TKRON1) and its varying-A batched GEMM (TGEMM_A)
+ * are defined further down, as direct sums.
+ *
  * Three independent evaluations are provided:
  *   O1 "direct":   the multiple sum written out (Sec. 2.1 sums), O(n^4) / O(n^6)
  *   O2 "factored": one mode at a time in the order of Algorithm 1 (first the
@@ -166,8 +169,59 @@ ORACLE_API void oracle_kron3_factored_##SUF(char ta, char tb, char tc, int ma, i
     }                                                                                          \
 }
 
+/* The paper's two other interfaces (Sec. 3), as direct sums.
+ *
+ * TKRON1 (1-D, "almost a batched GEMV"):
+ *   y^p <- alpha * op(A) x^p + beta * y^p,  op(A): ma x na,
+ *   x^p: na contiguous elements at X + p*ldxp, y^p: ma at Y + p*ldyp.
+ *   (The printed interface names both vector strides "ldp"; they are read as
+ *   the X and the Y stride.)
+ *
+ * TGEMM_A (batched GEMM whose first factor varies across the batch):
+ *   C^p <- alpha * op(A^p) op(B) + beta * C^p,  op(A^p): m x k at A + p*lda2,
+ *   op(B): k x n (shared), C^p: m x n at C + p*ldc2, column stride ldc.
+ */
+#define DEFINE_ORACLE_1D_GEMM(T, SUF)                                                          \
+ORACLE_API void oracle_kron1_##SUF(char ta, int ma, int na, int64_t batch, T alpha,            \
+    const T* A, int lda, const T* X, int64_t ldxp, T beta, T* Y, int64_t ldyp)                  \
+{                                                                                              \
+    int64_t p;                                                                                 \
+    _Pragma("omp parallel for schedule(static)")                                               \
+    for (p = 0; p < batch; p++) {                                                              \
+        const T* xp = X + p * ldxp;                                                            \
+        T* yp = Y + p * ldyp;                                                                  \
+        for (int i = 0; i < ma; i++) {                                                         \
+            T s = 0;                                                                           \
+            for (int l = 0; l < na; l++) s += OPEL(A, lda, ta, i, l) * xp[l];                  \
+            yp[i] = (beta == (T)0) ? alpha * s : alpha * s + beta * yp[i];                     \
+        }                                                                                      \
+    }                                                                                          \
+}                                                                                              \
+                                                                                               \
+ORACLE_API void oracle_gemm_a_##SUF(char ta, char tb, int m, int n, int k, T alpha,            \
+    const T* A, int lda, int64_t lda2, const T* B, int ldb, T beta, T* C, int ldc,              \
+    int64_t ldc2, int64_t batch)                                                               \
+{                                                                                              \
+    int64_t p;                                                                                 \
+    _Pragma("omp parallel for schedule(static)")                                               \
+    for (p = 0; p < batch; p++) {                                                              \
+        const T* Ap = A + p * lda2;                                                            \
+        T* Cp = C + p * ldc2;                                                                  \
+        for (int j = 0; j < n; j++)                                                            \
+            for (int i = 0; i < m; i++) {                                                      \
+                T s = 0;                                                                       \
+                for (int l = 0; l < k; l++)                                                    \
+                    s += OPEL(Ap, lda, ta, i, l) * OPEL(B, ldb, tb, l, j);                     \
+                T* c = &Cp[(size_t)i + (size_t)ldc * j];                                       \
+                *c = (beta == (T)0) ? alpha * s : alpha * s + beta * *c;                       \
+            }                                                                                  \
+    }                                                                                          \
+}
+
 DEFINE_ORACLE(double, f64)
 DEFINE_ORACLE(float, f32)
+DEFINE_ORACLE_1D_GEMM(double, f64)
+DEFINE_ORACLE_1D_GEMM(float, f32)
 
 /* O3: the Kronecker matrix K = A (x) B from the block definition of Sec. 2:
  * block (r, c) of K is a_{rc} * B, so K[r*mb + i, c*nb + j] = A[r,c] * B[i,j].
