@@ -343,6 +343,96 @@ def measure_variant(kg, name, steps, warmup, torch, dev, peaks, tune=True):
     return r
 
 
+def _time_calls(fn, steps, warmup, torch):
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        fn()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for i in range(steps):
+        ev[i][0].record(stream)
+        fn()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(c) for a, c in ev) / steps
+
+
+def measure_interfaces(kg, steps, warmup, torch, dev, peaks):
+    """The paper's other two interfaces (Sec. 3) and its unfused 3-D algorithm
+    (Algorithm 1: the 2-D product on every plane into tmp in HBM, then TGEMM_A
+    for the third mode), next to the fused 3-D kernel.  FP32, inputs > L2."""
+    import oracle
+    out = {}
+    rng = np.random.default_rng(21)
+
+    def line(ms, fl, by, kernel, err, extra=None):
+        gbs = by / (ms * 1e-3) / 1e9
+        r = {"gflops": round(fl / (ms * 1e-3) / 1e9, 1), "hbm_gbs": round(gbs, 1),
+             "hbm_frac": round(gbs / peaks["hbm"], 4), "ms": round(ms, 4), "kernel": kernel,
+             "max_norm_err_vs_fp64_oracle": err}
+        r.update(extra or {})
+        return r
+
+    # TGEMM_A at the shape Algorithm 1 gives it for n = 16: m = n^2, k = n = 16
+    m, n, k, batch = 256, 16, 16, 1 << 16
+    A = torch.randn(batch * m * k, device=dev)
+    B = rng.uniform(-1, 1, (k, n)).astype(np.float32)
+    C = torch.empty(batch * m * n, device=dev)
+    ms = _time_calls(lambda: kg.gemm_a_batched(A, B, C, m=m, n=n, k=k, batch=batch), steps, warmup, torch)
+    idx = np.sort(rng.choice(batch, 128, replace=False))
+    As = A.view(batch, -1)[torch.from_numpy(idx).to(dev)].double().cpu().numpy()
+    ref = oracle.gemm_a(As.ravel(), np.ascontiguousarray(B.T).ravel().astype(np.float64), m=m, n=n, k=k,
+                        batch=len(idx))
+    got = C.view(batch, -1)[torch.from_numpy(idx).to(dev)].double().cpu().numpy().ravel()
+    err = float((np.abs(got - ref).reshape(len(idx), -1).max(axis=1) /
+                 (np.linalg.norm(As, axis=1) * np.linalg.norm(B))).max())
+    out["tgemm_a-f32-m256-n16-k16"] = line(ms, 2.0 * m * n * k * batch, 4.0 * (m * k + m * n) * batch,
+                                           "gemm_a_kernel<f32,n=16>", err, {"batch": batch})
+    del A, C
+
+    # TKRON1, n = 16
+    nn, batch = 16, 1 << 24
+    A1 = rng.uniform(-1, 1, (nn, nn)).astype(np.float32)
+    X = torch.randn(batch * nn, device=dev)
+    Y = torch.empty_like(X)
+    ms = _time_calls(lambda: kg.kron1_batched(A1, X, Y, ma=nn, na=nn, batch=batch), steps, warmup, torch)
+    idx = np.sort(rng.choice(batch, 1024, replace=False))
+    Xs = X.view(batch, -1)[torch.from_numpy(idx).to(dev)].double().cpu().numpy()
+    ref = oracle.kron1(np.ascontiguousarray(A1.T).ravel().astype(np.float64), Xs.ravel(), ma=nn, na=nn,
+                       batch=len(idx))
+    got = Y.view(batch, -1)[torch.from_numpy(idx).to(dev)].double().cpu().numpy().ravel()
+    err = float((np.abs(got - ref).reshape(len(idx), -1).max(axis=1) /
+                 (np.linalg.norm(Xs, axis=1) * np.linalg.norm(A1))).max())
+    out["tkron1-f32-n16"] = line(ms, 2.0 * nn * nn * batch, 8.0 * nn * batch, "gemm_a_kernel<f32,n=16> (m = 1)",
+                                 err, {"batch": batch})
+    del X, Y
+
+    # Algorithm 1 (unfused 3-D) next to the fused kernel, same data
+    for n3, batch in ((16, 1 << 16), (10, 1 << 18)):
+        from paper_1304_7054_gb300 import inputs
+        b = inputs.make_batch(3, n3, batch, seed=3, x_dist="normal", dtype=np.float32)
+        X = torch.from_numpy(b.X).to(dev)
+        tmp = torch.empty_like(X)
+        Y = torch.empty_like(X)
+
+        def unfused():
+            kg.kron2_batched(b.B, b.C, X, tmp, ma=n3, na=n3, mb=n3, nb=n3, batch=batch * n3)
+            kg.gemm_a_batched(tmp, b.A, Y, m=n3 * n3, n=n3, k=n3, batch=batch, transb="T", lda=n3 * n3,
+                              lda2=n3 ** 3, ldc=n3 * n3, ldc2=n3 ** 3)
+        ms_u = _time_calls(unfused, steps, warmup, torch)
+        err = sample_error(kg, b, Y, "f32", torch)
+        ms_f = _time_calls(lambda: call(kg, b, X, Y, "native"), steps, warmup, torch)
+        fl = flops_per_instance(3, n3) * batch
+        by = 2 * 4 * n3 ** 3 * batch
+        out[f"kron3-f32-n{n3}-unfused-algorithm1"] = line(
+            ms_u, fl, by, "pair2ip/pair16/pair_kernel (2-D on planes) + gemm_a_kernel", err,
+            {"batch": batch, "hbm_bytes_moved": 2 * by, "hbm_gbs_moved": round(2 * by / (ms_u * 1e-3) / 1e9, 1),
+             "fused_kernel_ms": round(ms_f, 4), "unfused_over_fused_time": round(ms_u / ms_f, 3)})
+        del X, tmp, Y
+    torch.cuda.empty_cache()
+    return out
+
+
 def kernel_of(kind, n, io, compute):
     """Name of the kernel the library dispatches a contiguous batch to."""
     if compute == "bf16x3":
@@ -504,6 +594,7 @@ def run_ours(args):
             for io in ("f32", "bf16"):
                 variants[f"varlen-{io}"] = measure_varlen(kg, io, max(5, min(args.steps, 30)), 3, torch, dev,
                                                           peaks)
+            variants.update(measure_interfaces(kg, max(5, min(args.steps, 30)), 3, torch, dev, peaks))
         cpu = cpu_baseline(b, seconds=args.cpu_seconds)
         out = {
             "metric": METRIC, "value": round(value, 1), "unit": "GFlop/s", "n_gpus": world,

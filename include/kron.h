@@ -139,6 +139,59 @@ KRON_API kron_status kron3_batched(kron_stream_t stream, char transa, char trans
                                    kron_compute comp);
 
 /*
+ * kron1_batched -- the paper's TKRON1 (Sec. 3), the 1-D product ("almost a
+ * batched GEMV"):
+ *
+ *   y^p <- alpha op(A) x^p + beta y^p,  p = 0 .. batch_count-1
+ *
+ *   op(A): ma x na (1 <= ma, na <= 16), stored as A, host pointer (FP64 for
+ *          KRON_R64F, FP32 otherwise), lda >= ma if transa = 'N', >= na if 'T'
+ *   x^p:   na contiguous elements at X + p*ldxp (device), ldxp >= 0
+ *   y^p:   ma contiguous elements at Y + p*ldyp (device), ldyp >= ma when
+ *          batch_count > 1 (outputs may not overlap)
+ *
+ * The paper prints both vector strides under one name; they are read as the X
+ * and the Y stride.  alpha, beta: host scalars of the compute type; beta = 0
+ * means Y is not read.  Storage: any kron_dtype; compute: KRON_COMPUTE_NATIVE
+ * only (KRON_ERR_NOT_SUPPORTED otherwise).  Errors: KRON_ERR_INVALID_VALUE
+ * (bad size, ld, stride, trans, null pointer with batch_count > 0),
+ * KRON_ERR_ALIAS (X and Y ranges overlap), KRON_ERR_CUDA.  batch_count = 0 is a
+ * no-op.  It runs on the kron_gemm_a_batched kernel with m = 1.
+ */
+KRON_API kron_status kron1_batched(kron_stream_t stream, char transa, int ma, int na, int64_t batch_count,
+                                   const void* alpha, const void* A, int lda, const void* X, int64_t ldxp,
+                                   const void* beta, void* Y, int64_t ldyp, kron_dtype io,
+                                   kron_compute comp);
+
+/*
+ * kron_gemm_a_batched -- the paper's TGEMM_A (Sec. 3): a batched GEMM whose
+ * first factor varies across the batch and whose second is shared,
+ *
+ *   C^p <- alpha op(A^p) op(B) + beta C^p,  p = 0 .. batch_count-1
+ *
+ *   op(A^p): m x k (1 <= m <= 2^24, 1 <= k <= 16) at A + p*lda2 (device),
+ *            column stride lda >= m if transa = 'N', >= k if 'T'; lda2 >= 0
+ *            (instances of A may overlap; 0 repeats one matrix)
+ *   op(B):   k x n (1 <= n <= 16), stored as B, host pointer (FP64 for
+ *            KRON_R64F, FP32 otherwise), ldb >= k if transb = 'N', >= n if 'T'
+ *   C^p:     m x n at C + p*ldc2 (device), column stride ldc >= m,
+ *            ldc2 >= ldc*(n-1) + m when batch_count > 1
+ *   grid_size: CTAs to launch; 0 = one persistent wave (the paper's interface
+ *            carries the same launch knob)
+ *
+ * The paper uses it for the third mode of its 3-D algorithm (Algorithm 1):
+ * with tmp^p the (mc mb) x na result of the 2-D product on every plane,
+ * Y^p = tmp^p op(A)^T.  Storage: any kron_dtype; compute: KRON_COMPUTE_NATIVE
+ * only.  Errors as kron1_batched (KRON_ERR_ALIAS when the A and C ranges
+ * overlap).
+ */
+KRON_API kron_status kron_gemm_a_batched(kron_stream_t stream, char transa, char transb, int m, int n, int k,
+                                         const void* alpha, const void* A, int lda, int64_t lda2,
+                                         const void* B, int ldb, const void* beta, void* C, int ldc,
+                                         int64_t ldc2, int64_t batch_count, int grid_size, kron_dtype io,
+                                         kron_compute comp);
+
+/*
  * kron_device_status -- synchronises `stream`, then reads and clears the
  * device status word of the current device.  Returns KRON_OK, or
  * KRON_ERR_DEVICE_TIMEOUT if a kernel gave up on a bounded wait since the last

@@ -36,6 +36,9 @@ SIGNATURES = {
                        _I, _I], _I),
     "kron3_batched": ([_P, _C, _C, _C, _I, _I, _I, _I, _I, _I, _L, _P, _P, _I, _P, _I, _P, _I, _P, _I, _I,
                        _L, _P, _P, _I, _I, _L, _I, _I], _I),
+    "kron1_batched": ([_P, _C, _I, _I, _L, _P, _P, _I, _P, _L, _P, _P, _L, _I, _I], _I),
+    "kron_gemm_a_batched": ([_P, _C, _C, _I, _I, _I, _P, _P, _I, _L, _P, _I, _P, _P, _I, _L, _L, _I, _I, _I],
+                            _I),
     "kron_device_status": ([_P], _I),
     "kron_set_tile_config": ([_I, _I, _I, _I, _I, _I], _I),
     "kron_get_tile_config": ([_I, _I, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
@@ -173,6 +176,49 @@ def kron3_batched(A, B, C, X, Y, *, ma, na, mb, nb, mc, nc, batch, alpha=1.0, be
                          io, COMPUTE[compute])
     _check(st, "kron3_batched")
     return Y
+
+
+def kron1_batched(A, X, Y, *, ma, na, batch, alpha=1.0, beta=0.0, transa="N", lda=None, ldxp=None, ldyp=None,
+                  compute="native", stream=None):
+    """TKRON1: y^p <- alpha op(A) x^p + beta y^p on CUDA tensors X, Y; A a host array."""
+    L = load_library()
+    io = _io_of(X)
+    if _io_of(Y) != io:
+        raise TypeError("X and Y must have the same dtype")
+    ctype = np.float64 if io == DTYPES["f64"] else np.float32
+    Ab, lda0 = _comp_buffer(A, ctype)
+    ta = transa.upper()
+    lda = lda or lda0 or (ma if ta == "N" else na)
+    ldxp = na if ldxp is None else ldxp
+    ldyp = ma if ldyp is None else ldyp
+    al, be = _scalar(alpha, ctype), _scalar(beta, ctype)
+    st = L.kron1_batched(_stream_handle(stream), ta.encode(), ma, na, batch, ctypes.addressof(al), Ab.ctypes.data,
+                         lda, X.data_ptr(), ldxp, ctypes.addressof(be), Y.data_ptr(), ldyp, io, COMPUTE[compute])
+    _check(st, "kron1_batched")
+    return Y
+
+
+def gemm_a_batched(A, B, C, *, m, n, k, batch, alpha=1.0, beta=0.0, transa="N", transb="N", lda=None, lda2=None,
+                   ldb=None, ldc=None, ldc2=None, grid_size=0, compute="native", stream=None):
+    """TGEMM_A: C^p <- alpha op(A^p) op(B) + beta C^p on CUDA tensors A, C; B a host array."""
+    L = load_library()
+    io = _io_of(A)
+    if _io_of(C) != io:
+        raise TypeError("A and C must have the same dtype")
+    ctype = np.float64 if io == DTYPES["f64"] else np.float32
+    Bb, ldb0 = _comp_buffer(B, ctype)
+    ta, tb = transa.upper(), transb.upper()
+    lda = lda or (m if ta == "N" else k)
+    lda2 = lda * (k if ta == "N" else m) if lda2 is None else lda2
+    ldb = ldb or ldb0 or (k if tb == "N" else n)
+    ldc = ldc or m
+    ldc2 = ldc * n if ldc2 is None else ldc2
+    al, be = _scalar(alpha, ctype), _scalar(beta, ctype)
+    st = L.kron_gemm_a_batched(_stream_handle(stream), ta.encode(), tb.encode(), m, n, k, ctypes.addressof(al),
+                               A.data_ptr(), lda, lda2, Bb.ctypes.data, ldb, ctypes.addressof(be), C.data_ptr(),
+                               ldc, ldc2, batch, grid_size, io, COMPUTE[compute])
+    _check(st, "kron_gemm_a_batched")
+    return C
 
 
 def device_status(stream=None) -> int:

@@ -225,6 +225,104 @@ KRON_API kron_status kron2_batched(kron_stream_t stream, char transa, char trans
     return dispatch(d, (cudaStream_t)stream);
 }
 
+static double host_scalar(const void* v, kron_dtype io) {
+    return io == KRON_R64F ? *static_cast<const double*>(v) : (double)*static_cast<const float*>(v);
+}
+
+static double host_elem(const void* M, size_t idx, kron_dtype io) {
+    return io == KRON_R64F ? static_cast<const double*>(M)[idx] : (double)static_cast<const float*>(M)[idx];
+}
+
+KRON_API kron_status kron_gemm_a_batched(kron_stream_t stream, char transa, char transb, int m, int n, int k,
+                                         const void* alpha, const void* A, int lda, int64_t lda2, const void* B,
+                                         int ldb, const void* beta, void* C, int ldc, int64_t ldc2,
+                                         int64_t batch_count, int grid_size, kron_dtype io, kron_compute comp) {
+    int ta, tb;
+    if (!trans_flag(transa, &ta) || !trans_flag(transb, &tb)) return KRON_ERR_INVALID_VALUE;
+    if (m < 1 || m > (1 << 24) || !dim_ok(n) || !dim_ok(k)) return KRON_ERR_INVALID_VALUE;
+    if (batch_count < 0 || grid_size < 0 || lda2 < 0 || ldc2 < 0) return KRON_ERR_INVALID_VALUE;
+    kron_status st = check_modes(io, comp);
+    if (st != KRON_OK) return st;
+    if (comp != KRON_COMPUTE_NATIVE) return KRON_ERR_NOT_SUPPORTED;
+    if (lda < (ta ? k : m) || ldb < (tb ? n : k) || ldc < m) return KRON_ERR_INVALID_VALUE;
+    const int64_t cext = (int64_t)ldc * (n - 1) + m;   // elements spanned by one C^p
+    if (batch_count > 1 && ldc2 < cext) return KRON_ERR_INVALID_VALUE;   // instances of C may not overlap
+    if (!alpha || !beta) return KRON_ERR_INVALID_VALUE;
+    if (batch_count == 0) return KRON_OK;
+    if (!A || !B || !C) return KRON_ERR_INVALID_VALUE;
+    const size_t es = elem_size(io);
+    if (((uintptr_t)A) % es || ((uintptr_t)C) % es) return KRON_ERR_INVALID_VALUE;
+    const int64_t aext = ta ? (int64_t)lda * (m - 1) + k : (int64_t)lda * (k - 1) + m;
+    const size_t abytes = ((size_t)(batch_count - 1) * lda2 + aext) * es;
+    const size_t cbytes = ((size_t)(batch_count - 1) * ldc2 + cext) * es;
+    if (ranges_overlap(A, abytes, C, cbytes)) return KRON_ERR_ALIAS;
+    static thread_local GemmADesc g;
+    g = GemmADesc();
+    g.m = m;
+    g.n = n;
+    g.k = k;
+    for (int l = 0; l < k; ++l)
+        for (int j = 0; j < n; ++j)
+            g.b[l * 16 + j] = host_elem(B, tb ? (size_t)j + (size_t)ldb * l : (size_t)l + (size_t)ldb * j, io);
+    g.A = A;
+    g.C = C;
+    g.lda = lda;
+    g.ldc = ldc;
+    g.transa = ta;
+    g.lda2 = lda2;
+    g.ldc2 = ldc2;
+    g.batch = batch_count;
+    g.alpha = host_scalar(alpha, io);
+    g.beta = host_scalar(beta, io);
+    g.io = io;
+    g.grid = grid_size;
+    return launch_gemm_a(g, (cudaStream_t)stream);
+}
+
+KRON_API kron_status kron1_batched(kron_stream_t stream, char transa, int ma, int na, int64_t batch_count,
+                                   const void* alpha, const void* A, int lda, const void* X, int64_t ldxp,
+                                   const void* beta, void* Y, int64_t ldyp, kron_dtype io, kron_compute comp) {
+    int ta;
+    if (!trans_flag(transa, &ta)) return KRON_ERR_INVALID_VALUE;
+    if (!dim_ok(ma) || !dim_ok(na)) return KRON_ERR_INVALID_VALUE;
+    if (batch_count < 0 || ldxp < 0 || ldyp < 0) return KRON_ERR_INVALID_VALUE;
+    kron_status st = check_modes(io, comp);
+    if (st != KRON_OK) return st;
+    if (comp != KRON_COMPUTE_NATIVE) return KRON_ERR_NOT_SUPPORTED;
+    if (lda < (ta ? na : ma)) return KRON_ERR_INVALID_VALUE;
+    if (batch_count > 1 && ldyp < ma) return KRON_ERR_INVALID_VALUE;   // outputs may not overlap
+    if (!alpha || !beta) return KRON_ERR_INVALID_VALUE;
+    if (batch_count == 0) return KRON_OK;
+    if (!A || !X || !Y) return KRON_ERR_INVALID_VALUE;
+    const size_t es = elem_size(io);
+    if (((uintptr_t)X) % es || ((uintptr_t)Y) % es) return KRON_ERR_INVALID_VALUE;
+    const size_t xbytes = ((size_t)(batch_count - 1) * ldxp + na) * es;
+    const size_t ybytes = ((size_t)(batch_count - 1) * ldyp + ma) * es;
+    if (ranges_overlap(X, xbytes, Y, ybytes)) return KRON_ERR_ALIAS;
+    // y^p (1 x ma) = x^p (1 x na) op(A)^T: TGEMM_A with m = 1, x^p as the one row
+    // of A^p (column stride 1, instance stride ldxp) and the shared factor op(A)^T.
+    static thread_local GemmADesc g;
+    g = GemmADesc();
+    g.m = 1;
+    g.n = ma;
+    g.k = na;
+    for (int l = 0; l < na; ++l)
+        for (int j = 0; j < ma; ++j)
+            g.b[l * 16 + j] = host_elem(A, ta ? (size_t)l + (size_t)lda * j : (size_t)j + (size_t)lda * l, io);
+    g.A = X;
+    g.lda = 1;
+    g.lda2 = ldxp;
+    g.transa = 0;
+    g.C = Y;
+    g.ldc = 1;
+    g.ldc2 = ldyp;
+    g.batch = batch_count;
+    g.alpha = host_scalar(alpha, io);
+    g.beta = host_scalar(beta, io);
+    g.io = io;
+    return launch_gemm_a(g, (cudaStream_t)stream);
+}
+
 KRON_API kron_status kron3_batched(kron_stream_t stream, char transa, char transb, char transc, int ma, int na,
                                    int mb, int nb, int mc, int nc, int64_t batch_count, const void* alpha,
                                    const void* A, int lda, const void* B, int ldb, const void* C, int ldc,

@@ -83,6 +83,22 @@ kron_status launch_pair16(const KronDesc& d, cudaStream_t s);
 // multiple of 8 instances); KRON_ERR_NOT_SUPPORTED otherwise.
 kron_status launch_pair2ip(const KronDesc& d, cudaStream_t s);
 
+// Batched GEMM with a varying first factor (TGEMM_A), after validation; the 1-D
+// product (TKRON1) is the case m = 1.
+struct GemmADesc {
+    int m = 1, n = 1, k = 1;
+    double b[16 * 16];       // op(B): b[l * 16 + j], l < k, j < n
+    const void* A = nullptr;
+    void* C = nullptr;
+    int lda = 1, ldc = 1;
+    int transa = 0;          // op(A^p)(i, l) at i + lda l (0) or l + lda i (1)
+    int64_t lda2 = 0, ldc2 = 0, batch = 0;
+    double alpha = 1.0, beta = 0.0;
+    kron_dtype io = KRON_R32F;
+    int grid = 0;            // CTAs; 0 = one persistent wave
+};
+kron_status launch_gemm_a(const GemmADesc& g, cudaStream_t s);
+
 // Tensor-core split-precision kernels (R32F or R16BF storage).
 kron_status launch_tc(const KronDesc& d, cudaStream_t s);
 

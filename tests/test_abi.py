@@ -95,3 +95,51 @@ def test_kron3_validation(lib, over, code):
         assert r != INVALID and r != NOTSUP   # valid arguments: only the launch itself can fail here
     else:
         assert r == code
+
+
+def k1(lib, **over):
+    a = dict(stream=None, ta=b"N", ma=4, na=5, batch=10, alpha=ctypes.addressof(F), A=COMP.ctypes.data, lda=4,
+             X=0x10000, ldxp=5, beta=ctypes.addressof(ZERO), Y=0x90000, ldyp=4, io=0, comp=0)
+    a.update(over)
+    return lib.kron1_batched(*a.values())
+
+
+def ga(lib, **over):
+    a = dict(stream=None, ta=b"N", tb=b"N", m=100, n=6, k=5, alpha=ctypes.addressof(F), A=0x10000, lda=100,
+             lda2=500, B=COMP.ctypes.data, ldb=5, beta=ctypes.addressof(ZERO), C=0x900000, ldc=100, ldc2=600,
+             batch=10, grid=0, io=0, comp=0)
+    a.update(over)
+    return lib.kron_gemm_a_batched(*a.values())
+
+
+@pytest.mark.parametrize("over,code", [
+    (dict(ma=0), INVALID), (dict(na=17), INVALID), (dict(ta=b"X"), INVALID), (dict(batch=-1), INVALID),
+    (dict(lda=3), INVALID), (dict(ta=b"T", lda=4), INVALID), (dict(ldyp=3), INVALID), (dict(ldxp=-1), INVALID),
+    (dict(alpha=None), INVALID), (dict(A=None), INVALID), (dict(X=None), INVALID), (dict(Y=None), INVALID),
+    (dict(io=7), INVALID), (dict(comp=1), NOTSUP), (dict(io=2, comp=1), NOTSUP),
+    (dict(Y=0x10000 + 4 * 40), ALIAS), (dict(X=0x10002), INVALID),
+    (dict(batch=0, X=None, Y=None), 0), (dict(batch=1, ldyp=0), "launch"),
+])
+def test_kron1_validation(lib, over, code):
+    r = k1(lib, **over)
+    if code == "launch":
+        assert r not in (INVALID, NOTSUP, ALIAS)
+    else:
+        assert r == code
+
+
+@pytest.mark.parametrize("over,code", [
+    (dict(m=0), INVALID), (dict(m=(1 << 24) + 1), INVALID), (dict(n=17), INVALID), (dict(k=0), INVALID),
+    (dict(ta=b"Z"), INVALID), (dict(tb=b"Z"), INVALID), (dict(lda=99), INVALID), (dict(ta=b"T", lda=4), INVALID),
+    (dict(ldb=4), INVALID), (dict(tb=b"T", ldb=5), INVALID), (dict(ldc=99), INVALID), (dict(ldc2=599), INVALID),
+    (dict(lda2=-1), INVALID), (dict(grid=-1), INVALID), (dict(batch=-1), INVALID), (dict(beta=None), INVALID),
+    (dict(B=None), INVALID), (dict(C=None), INVALID), (dict(comp=1), NOTSUP),
+    (dict(C=0x10000 + 4 * 4000), ALIAS), (dict(C=0x900002), INVALID),
+    (dict(batch=0, A=None, C=None), 0), (dict(lda2=0), "launch"), (dict(batch=1, ldc2=0), "launch"),
+])
+def test_gemm_a_validation(lib, over, code):
+    r = ga(lib, **over)
+    if code == "launch":
+        assert r not in (INVALID, NOTSUP, ALIAS)
+    else:
+        assert r == code
