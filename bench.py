@@ -403,7 +403,7 @@ def measure_interfaces(kg, steps, warmup, torch, dev, peaks):
     got = Y.view(batch, -1)[torch.from_numpy(idx).to(dev)].double().cpu().numpy().ravel()
     err = float((np.abs(got - ref).reshape(len(idx), -1).max(axis=1) /
                  (np.linalg.norm(Xs, axis=1) * np.linalg.norm(A1))).max())
-    out["tkron1-f32-n16"] = line(ms, 2.0 * nn * nn * batch, 8.0 * nn * batch, "gemm_a_kernel<f32,n=16> (m = 1)",
+    out["tkron1-f32-n16"] = line(ms, 2.0 * nn * nn * batch, 8.0 * nn * batch, "kron1_kernel<f32,n=16>",
                                  err, {"batch": batch})
     del X, Y
 

@@ -81,6 +81,7 @@ FAMILY_SOURCES = {
     "pair2ip_kernel": ["kron_pair2ip.cu", "kron_pair.cuh", "kron_fiber.cuh", "kron_device.cuh"],
     "fiber_kernel": ["kron_fiber.cuh", "kron_device.cuh"],
     "gemm_a_kernel": ["kron_gemm_a.cu", "kron_pair.cuh", "kron_fiber.cuh", "kron_device.cuh"],
+    "kron1_kernel": ["kron_kron1.cu", "kron_pair.cuh", "kron_fiber.cuh", "kron_device.cuh"],
     "tc2_kernel": ["kron_tc.cu", "kron_fiber.cuh", "kron_device.cuh"],
     "tc3_kernel": ["kron_tc.cu", "kron_fiber.cuh", "kron_device.cuh"],
     "varlen_kernel": ["kron_varlen.cu", "kron_fiber.cuh", "kron_device.cuh"],

@@ -320,7 +320,8 @@ KRON_API kron_status kron1_batched(kron_stream_t stream, char transa, int ma, in
     g.alpha = host_scalar(alpha, io);
     g.beta = host_scalar(beta, io);
     g.io = io;
-    return launch_gemm_a(g, (cudaStream_t)stream);
+    const kron_status r = launch_kron1(g, (cudaStream_t)stream);
+    return r == KRON_ERR_NOT_SUPPORTED ? launch_gemm_a(g, (cudaStream_t)stream) : r;
 }
 
 KRON_API kron_status kron3_batched(kron_stream_t stream, char transa, char transb, char transc, int ma, int na,

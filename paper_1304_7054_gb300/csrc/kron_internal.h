@@ -98,6 +98,9 @@ struct GemmADesc {
     int grid = 0;            // CTAs; 0 = one persistent wave
 };
 kron_status launch_gemm_a(const GemmADesc& g, cudaStream_t s);
+// TKRON1 given as that descriptor with m = 1 (FP32 / 16-bit storage);
+// KRON_ERR_NOT_SUPPORTED otherwise.
+kron_status launch_kron1(const GemmADesc& g, cudaStream_t s);
 
 // Tensor-core split-precision kernels (R32F or R16BF storage).
 kron_status launch_tc(const KronDesc& d, cudaStream_t s);
