@@ -106,6 +106,16 @@ def test_gemm_a_small_grids_walk_every_row(grid_size, m):
     assert ga_case("f32", m, 4, 3, "N", "N", batch=29, grid_size=grid_size, seed=m) <= TOL["f32"]
 
 
+@pytest.mark.parametrize("m,n,k", [(32, 16, 16), (64, 8, 12), (256, 16, 16), (100, 15, 16), (1536, 4, 16)])
+@pytest.mark.parametrize("grid_size", [0, 1, 3])
+@pytest.mark.parametrize("alpha,beta", [(1.0, 0.0), (-0.5, 1.5)])
+def test_gemm_a_packed_batches(m, n, k, grid_size, alpha, beta):
+    """Packed FP32 batches (contiguous A^p and C^p, the layout of the paper's
+    Algorithm 1) with grids smaller than the row count and alpha / beta."""
+    assert ga_case("f32", m, n, k, "N", "N", batch=37, alpha=alpha, beta=beta, grid_size=grid_size,
+                   seed=m + n) <= 2 * TOL["f32"]
+
+
 @pytest.mark.parametrize("io", ["f32", "f64", "bf16"])
 def test_gemm_a_identity_is_exact(io):
     torch = _torch()
