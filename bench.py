@@ -659,6 +659,26 @@ def run_profile(args):
                           "gflops": fl / (ms * 1e-3) / 1e9, "hbm_gbs": by / (ms * 1e-3) / 1e9}))
         plan.close()
         return
+    if args.workload in ("tkron1-f32-n16", "tgemm_a-f32-m256-n16-k16"):
+        rng = np.random.default_rng(21)
+        if args.workload == "tkron1-f32-n16":
+            batch = args.batch or (1 << 24)
+            A1 = rng.uniform(-1, 1, (16, 16)).astype(np.float32)
+            X = torch.randn(batch * 16, device=dev)
+            Y = torch.empty_like(X)
+            fn = lambda: kg.kron1_batched(A1, X, Y, ma=16, na=16, batch=batch)
+            fl, by = 2.0 * 256 * batch, 8.0 * 16 * batch
+        else:
+            batch = args.batch or (1 << 16)
+            A = torch.randn(batch * 256 * 16, device=dev)
+            B = rng.uniform(-1, 1, (16, 16)).astype(np.float32)
+            C = torch.empty_like(A)
+            fn = lambda: kg.gemm_a_batched(A, B, C, m=256, n=16, k=16, batch=batch)
+            fl, by = 2.0 * 256 * 16 * 16 * batch, 4.0 * 2 * 256 * 16 * batch
+        kern_ms = _time_calls(fn, args.steps, args.warmup, torch)
+        print(json.dumps({"workload": args.workload, "batch": batch, "kernel_ms": kern_ms,
+                          "gflops": fl / (kern_ms * 1e-3) / 1e9, "hbm_gbs": by / (kern_ms * 1e-3) / 1e9}))
+        return
     wl = WORKLOADS[args.workload]
     b = make_inputs(wl)
     X = to_device_storage(b, wl["io"], torch, dev)
@@ -732,13 +752,16 @@ def main():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["varlen-f32", "varlen-bf16"], default=HEADLINE)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["varlen-f32", "varlen-bf16", "tkron1-f32-n16",
+                                                               "tgemm_a-f32-m256-n16-k16"], default=HEADLINE)
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=8.0)
     ap.add_argument("--batch", type=int, default=0, help="override the batch (profiling a smaller case)")
     ap.add_argument("--profile", action="store_true",
                     help="only warm-up + timed steps of the workload, no extra legs (for ncu captures)")
     args = ap.parse_args()
+    if args.workload not in WORKLOADS and not args.profile:
+        ap.error(f"--workload {args.workload} is measured as a variant of the default run; alone it needs --profile")
     if args.warmup < 3:
         args.warmup = 3
     if args.batch:
