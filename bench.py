@@ -387,7 +387,7 @@ def measure_interfaces(kg, steps, warmup, torch, dev, peaks):
     err = float((np.abs(got - ref).reshape(len(idx), -1).max(axis=1) /
                  (np.linalg.norm(As, axis=1) * np.linalg.norm(B))).max())
     out["tgemm_a-f32-m256-n16-k16"] = line(ms, 2.0 * m * n * k * batch, 4.0 * (m * k + m * n) * batch,
-                                           "gemm_a_kernel<f32,n=16>", err, {"batch": batch})
+                                           "gemm_a_pair_kernel<f32,n=16>", err, {"batch": batch})
     del A, C
 
     # TKRON1, n = 16

@@ -11,12 +11,19 @@
 // pair kernels -- and stores the outputs column by column (coalesced across
 // threads again).  FP64 uses plain double FMAs.  The grid is persistent and
 // walks rows p * m + i with a stride kept as (instances, rows) so that no
-// division is needed inside the loop.
+// division is needed inside the loop.  With op = 'N' and even strides a thread
+// takes a pair of rows instead (see gemm_a_pair_kernel).
 #include "kron_pair.cuh"
 
 namespace kron {
 
 namespace {
+
+inline unsigned __float_as_uint_host(float v) {
+    unsigned b;
+    memcpy(&b, &v, sizeof(b));
+    return b;
+}
 
 constexpr int kGaThreads = 256;
 constexpr int kGaMaxK = 16;
@@ -79,6 +86,119 @@ __global__ void __launch_bounds__(kGaThreads) gemm_a_kernel(const __grid_constan
             ++p;
         }
     }
+}
+
+// Pairs of rows (op = 'N', even m and strides): rows (i, i+1) of op(A^p) are
+// adjacent in memory, so one thread loads both as a pair, multiplies them by
+// the duplicated coefficient (B[l, j], B[l, j]) -- a constant operand -- and
+// stores the two results of column j as a pair.  Half the address arithmetic
+// of the one-row kernel and no operand duplication.
+template <int NN>
+struct __align__(8) GemmA2Args {
+    f2 bd[kGaMaxK * NN];   // (B[l, j], B[l, j]) at l * NN + j, zero beyond k x n
+    const void* A;
+    void* C;
+    int64_t lda2, ldc2, batch;
+    int64_t step_p;        // grid stride = step_p instances + step_i row pairs
+    int step_i;
+    int lda, ldc, m2, n, k;
+    int beta_zero, alpha_one;
+    float alpha, beta;
+};
+
+template <typename S, int NN>
+__global__ void __launch_bounds__(kGaThreads) gemm_a_pair_kernel(const __grid_constant__ GemmA2Args<NN> a) {
+    const int64_t r0 = (int64_t)blockIdx.x * kGaThreads + threadIdx.x;
+    int64_t p = r0 / a.m2;
+    int i2 = (int)(r0 - p * a.m2);
+    const S* A = static_cast<const S*>(a.A);
+    S* C = static_cast<S*>(a.C);
+    while (p < a.batch) {
+        const S* ar = A + p * a.lda2 + 2 * i2;
+        f2 x[kGaMaxK];
+#pragma unroll
+        for (int l = 0; l < kGaMaxK; ++l) x[l] = l < a.k ? load_pair<S>(ar + (int64_t)a.lda * l) : 0ull;
+        f2 c[NN];
+#pragma unroll
+        for (int j = 0; j < NN; ++j) c[j] = fmul2(a.bd[j], x[0]);
+#pragma unroll
+        for (int l = 1; l < kGaMaxK; ++l) {
+            if (l < a.k) {
+#pragma unroll
+                for (int j = 0; j < NN; ++j) c[j] = ffma2(a.bd[l * NN + j], x[l], c[j]);
+            }
+        }
+        S* cr = C + p * a.ldc2 + 2 * i2;
+        const f2 al = f2_pack(a.alpha, a.alpha), be = f2_pack(a.beta, a.beta);
+#pragma unroll
+        for (int j = 0; j < NN; ++j) {
+            if (j < a.n) {
+                f2 v = a.alpha_one ? c[j] : fmul2(c[j], al);
+                S* dst = cr + (int64_t)a.ldc * j;
+                if (!a.beta_zero) v = ffma2(be, load_pair<S>(dst), v);
+                if constexpr (sizeof(S) == 4)
+                    *reinterpret_cast<f2*>(dst) = v;
+                else
+                    *reinterpret_cast<unsigned*>(dst) = pack16<S>(v);
+            }
+        }
+        i2 += a.step_i;
+        p += a.step_p;
+        if (i2 >= a.m2) {
+            i2 -= a.m2;
+            ++p;
+        }
+    }
+}
+
+template <typename S, int NN>
+kron_status launch_ga_pair(const GemmADesc& g, cudaStream_t st) {
+    GemmA2Args<NN> a;
+    memset(&a, 0, sizeof(a));
+    for (int l = 0; l < g.k; ++l)
+        for (int j = 0; j < g.n; ++j) {
+            const float v = (float)g.b[l * kGaMaxK + j];
+            a.bd[l * NN + j] = ((f2)__float_as_uint_host(v) << 32) | (f2)__float_as_uint_host(v);
+        }
+    a.A = g.A;
+    a.C = g.C;
+    a.lda2 = g.lda2;
+    a.ldc2 = g.ldc2;
+    a.batch = g.batch;
+    a.lda = g.lda;
+    a.ldc = g.ldc;
+    a.m2 = g.m / 2;
+    a.n = g.n;
+    a.k = g.k;
+    a.alpha = (float)g.alpha;
+    a.beta = (float)g.beta;
+    a.alpha_one = g.alpha == 1.0;
+    a.beta_zero = g.beta == 0.0;
+    const DeviceInfo& dev = device_info();
+    if (dev.sms <= 0) return KRON_ERR_CUDA;
+    auto kern = gemm_a_pair_kernel<S, NN>;
+    const int64_t units = g.batch * a.m2;
+    int64_t grid = g.grid;
+    if (grid <= 0) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGaThreads, 0) != cudaSuccess)
+            return KRON_ERR_CUDA;
+        grid = (int64_t)(per_sm < 1 ? 1 : per_sm) * dev.sms;
+    }
+    grid = std::max<int64_t>(1, std::min<int64_t>(grid, (units + kGaThreads - 1) / kGaThreads));
+    const int64_t step = grid * kGaThreads;
+    a.step_p = step / a.m2;
+    a.step_i = (int)(step % a.m2);
+    kern<<<(unsigned)grid, kGaThreads, 0, st>>>(a);
+    return cudaPeekAtLastError() == cudaSuccess ? KRON_OK : KRON_ERR_CUDA;
+}
+
+// Layouts the row-pair kernel takes: op = 'N', every row pair 2 * sizeof(S)-aligned.
+bool ga_pair_ok(const GemmADesc& g) {
+    if (g.io == KRON_R64F || g.transa || g.m % 2) return false;
+    const size_t es = elem_size(g.io);
+    return g.lda % 2 == 0 && g.lda2 % 2 == 0 && g.ldc % 2 == 0 && g.ldc2 % 2 == 0 &&
+           (uintptr_t)g.A % (2 * es) == 0 && (uintptr_t)g.C % (2 * es) == 0;
 }
 
 template <int NN>
@@ -165,6 +285,14 @@ kron_status launch_ga(const GemmADesc& g, Kern kern, cudaStream_t st) {
 
 template <int NN>
 kron_status launch_ga_nn(const GemmADesc& g, cudaStream_t st) {
+    if (ga_pair_ok(g)) {
+        switch (g.io) {
+            case KRON_R32F: return launch_ga_pair<float, NN>(g, st);
+            case KRON_R16BF: return launch_ga_pair<__nv_bfloat16, NN>(g, st);
+            case KRON_R16F: return launch_ga_pair<__half, NN>(g, st);
+            default: break;
+        }
+    }
     switch (g.io) {
         case KRON_R32F: return launch_ga<float, NN>(g, gemm_a_kernel<float, NN>, st);
         case KRON_R16BF: return launch_ga<float, NN>(g, gemm_a_kernel<__nv_bfloat16, NN>, st);
