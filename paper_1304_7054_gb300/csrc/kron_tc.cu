@@ -9,8 +9,9 @@
 // operand is exact (lo = 0) and its products with the split components need two
 // MMAs instead of three.
 //
-// 2-D (Y = M1 X M2^T, paper Sec. 2 vec identity), one warp per instance, sizes
-// n <= 16 zero-padded to 16:
+// 2-D (Y = M1 X M2^T, paper Sec. 2 vec identity), one warp per 16 x 16 tile:
+// one instance for n > 8 (zero-padded), two for 4 < n <= 8 and four for n <= 4
+// on the tile's diagonal:
 //   stage 1  W = M1 X       A = M1 (constant fragments), B = X (from the tile)
 //   stage 2  Y = W M2^T     A = W taken straight from the stage-1 accumulators
 //                           (the m16n8 accumulator layout of two n-tiles is the
@@ -78,8 +79,34 @@ __device__ __forceinline__ unsigned x_pair_bf16(const __nv_bfloat16* xq, int l, 
     }
 }
 
-template <typename S, int N>
-__device__ __forceinline__ void tc2_instance(const TcArgs2<N>& a, const S* xq, S* yq, const unsigned (&m1h)[4],
+// Small instances share one 16 x 16 tile: 16 / B instances of size n <= B sit
+// on its diagonal in B x B blocks, with blockdiag(M, ..., M) as the component.
+// Off-diagonal blocks stay zero through both products, so one tile computes
+// all of them with the MMAs of one instance.
+__host__ __device__ constexpr int tc2_block(int n) { return n <= 4 ? 4 : (n <= 8 ? 8 : 16); }
+
+// Element pair (l, l+1) x column m of the block-diagonal operand tile.
+template <typename S, int N, int B>
+__device__ __forceinline__ void x_pair_blk(const S* const (&xq)[16 / B], int l, int m, float& v0, float& v1) {
+    const int b = l / B;
+    if (b == m / B && xq[b]) {
+        x_pair<S, N>(xq[b], l % B, m % B, v0, v1);
+    } else {
+        v0 = 0.f;
+        v1 = 0.f;
+    }
+}
+
+template <int N, int B>
+__device__ __forceinline__ unsigned x_pair_bf16_blk(const __nv_bfloat16* const (&xq)[16 / B], int l, int m) {
+    const int b = l / B;
+    return (b == m / B && xq[b]) ? x_pair_bf16<N>(xq[b], l % B, m % B) : 0u;
+}
+
+// One 16 x 16 tile: 16 / B instances (xq[b] / yq[b], null when absent).
+template <typename S, int N, int B>
+__device__ __forceinline__ void tc2_instance(const TcArgs2<N>& a, const S* const (&xq)[16 / B],
+                                             S* const (&yq)[16 / B], const unsigned (&m1h)[4],
                                              const unsigned (&m1l)[4], const unsigned (&m2h)[2][2],
                                              const unsigned (&m2l)[2][2]) {
     const int lane = threadIdx.x & 31;
@@ -92,19 +119,19 @@ __device__ __forceinline__ void tc2_instance(const TcArgs2<N>& a, const S* xq, S
 #pragma unroll
         for (int e = 0; e < 4; ++e) w[nt][e] = 0.f;
         if constexpr (sizeof(S) == 2 && std::is_same<S, __nv_bfloat16>::value) {
-            const unsigned b0 = x_pair_bf16<N>(xq, 2 * t, m);
-            const unsigned b1 = x_pair_bf16<N>(xq, 2 * t + 8, m);
+            const unsigned b0 = x_pair_bf16_blk<N, B>(xq, 2 * t, m);
+            const unsigned b1 = x_pair_bf16_blk<N, B>(xq, 2 * t + 8, m);
             mma_bf16_16816(w[nt], m1l, b0, b1);
             mma_bf16_16816(w[nt], m1h, b0, b1);
         } else {
             float x0, x1, x2, x3;
             if constexpr (N == 16 && sizeof(S) == 4) {
-                const float2 p0 = *reinterpret_cast<const float2*>(xq + 2 * t + 16 * m);
-                const float2 p1 = *reinterpret_cast<const float2*>(xq + 2 * t + 8 + 16 * m);
+                const float2 p0 = *reinterpret_cast<const float2*>(xq[0] + 2 * t + 16 * m);
+                const float2 p1 = *reinterpret_cast<const float2*>(xq[0] + 2 * t + 8 + 16 * m);
                 x0 = p0.x; x1 = p0.y; x2 = p1.x; x3 = p1.y;
             } else {
-                x_pair<S, N>(xq, 2 * t, m, x0, x1);
-                x_pair<S, N>(xq, 2 * t + 8, m, x2, x3);
+                x_pair_blk<S, N, B>(xq, 2 * t, m, x0, x1);
+                x_pair_blk<S, N, B>(xq, 2 * t + 8, m, x2, x3);
             }
             unsigned bh0, bl0, bh1, bl1;
             split_pair(x0, x1, bh0, bl0);
@@ -130,8 +157,9 @@ __device__ __forceinline__ void tc2_instance(const TcArgs2<N>& a, const S* xq, S
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const int i = g + 8 * (e >> 1), jj = j + (e & 1);
-            if (i < N && jj < N) {
-                S* dst = yq + i + N * jj;
+            const int b = i / B, il = i % B, jl = jj % B;
+            if (b == jj / B && yq[b] && il < N && jl < N) {
+                S* dst = yq[b] + il + N * jl;
                 float v = a.alpha_one ? y[e] : a.alpha * y[e];
                 if (!a.beta_zero) v = fmaf(a.beta, load_cvt<float, S>(*dst), v);
                 if constexpr (sizeof(S) == 4)
@@ -206,8 +234,18 @@ __global__ void __launch_bounds__(kTcThreads) tc2_kernel(const __grid_constant__
             __syncthreads();
         }
         if (ok) {
-            for (int q = warp; q < cnt; q += kTcThreads / 32)
-                tc2_instance<S, N>(a, xt + q * NX, static_cast<S*>(a.Y) + (inst0 + q) * NX, m1h, m1l, m2h, m2l);
+            constexpr int B = tc2_block(N), PK = 16 / B;
+            for (int q0 = warp * PK; q0 < cnt; q0 += PK * (kTcThreads / 32)) {
+                const S* xq[PK];
+                S* yq[PK];
+#pragma unroll
+                for (int b = 0; b < PK; ++b) {
+                    const bool live = q0 + b < cnt;
+                    xq[b] = live ? xt + (q0 + b) * NX : nullptr;
+                    yq[b] = live ? static_cast<S*>(a.Y) + (inst0 + q0 + b) * NX : nullptr;
+                }
+                tc2_instance<S, N, B>(a, xq, yq, m1h, m1l, m2h, m2l);
+            }
         }
         if (__syncthreads_or(!ok)) {
             if (tid == 0) {
@@ -483,13 +521,16 @@ static inline float bf16_to_float(unsigned short h) {
 }
 
 // Column-major N x N (double) -> row-major 16 x 16 packed bf16 pairs, split hi/lo.
-static void split_rowmajor(const double* m, int N, unsigned* hi, unsigned* lo) {
+// Row-major 16 x 16 split of blockdiag(M, ..., M) with B x B blocks (B = 16:
+// M itself, zero-padded).
+static void split_rowmajor(const double* m, int N, unsigned* hi, unsigned* lo, int B = 16) {
     for (int r = 0; r < 16; ++r)
         for (int c2 = 0; c2 < 8; ++c2) {
             unsigned short h[2], l[2];
             for (int e = 0; e < 2; ++e) {
                 const int c = 2 * c2 + e;
-                const float v = (r < N && c < N) ? (float)m[r + N * c] : 0.f;
+                const int rl = r % B, cl = c % B;
+                const float v = (r / B == c / B && rl < N && cl < N) ? (float)m[rl + N * cl] : 0.f;
                 h[e] = bf16_rne(v);
                 l[e] = bf16_rne(v - bf16_to_float(h[e]));
             }
@@ -503,8 +544,8 @@ static kron_status launch_tc2_n(const KronDesc& d, cudaStream_t st) {
     const DeviceInfo& dev = device_info();
     if (dev.sms <= 0) return KRON_ERR_CUDA;
     TcArgs2<N> a;
-    split_rowmajor(d.m1, N, a.m1h, a.m1l);
-    split_rowmajor(d.m2, N, a.m2h, a.m2l);
+    split_rowmajor(d.m1, N, a.m1h, a.m1l, tc2_block(N));
+    split_rowmajor(d.m2, N, a.m2h, a.m2l, tc2_block(N));
     a.X = d.X;
     a.Y = d.Y;
     a.batch = d.batch;

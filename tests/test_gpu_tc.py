@@ -44,9 +44,10 @@ def test_bf16x3_2d_bf16_storage(n):
     assert err <= TOL["bf16"] + bound(2, n)
 
 
-def test_bf16x3_bf16_storage_identity_is_exact():
-    n = 16
-    b = inputs.make_batch(2, n, 200, seed=330)
+@pytest.mark.parametrize("n", [3, 4, 6, 8, 16])
+def test_bf16x3_bf16_storage_identity_is_exact(n):
+    """Small n share a tile (instances on its diagonal); identity stays exact."""
+    b = inputs.make_batch(2, n, 201, seed=330)
     b.A = np.eye(n).ravel(order="F").astype(np.float32)
     b.B = b.A.copy()
     Y, X64 = run_gpu(b, io="bf16", compute="bf16x3")
@@ -61,6 +62,19 @@ def test_bf16x3_alpha_beta(kind, n):
     Y, X64 = run_gpu(b, io="f32", compute="bf16x3", alpha=0.75, beta=-2.0, Y0=Y0, guard=8)
     ref = oracle_ref(b, X64, alpha=0.75, beta=-2.0, Y=Y0)
     assert max_norm_err(Y, ref, b, X64) <= 2 * bound(kind, n) + 1e-6
+
+
+@pytest.mark.parametrize("n", [3, 6, 8])
+@pytest.mark.parametrize("P,depth", [(3, 1), (7, 2), (33, 3)])
+def test_bf16x3_2d_packed_tiles_any_tile_size(n, P, depth):
+    """Odd tile sizes leave the last pair / quadruple of a tile half filled."""
+    b = inputs.make_batch(2, n, 1001, seed=350 + n + P, x_dist="normal")
+    try:
+        kg.set_tile_config(2, n, "f32", "bf16x3", P, depth)
+        Y, X64 = run_gpu(b, io="f32", compute="bf16x3", guard=16)
+    finally:
+        kg.set_tile_config(2, n, "f32", "bf16x3", 0, 0)
+    assert max_norm_err(Y, oracle_ref(b, X64), b, X64) <= 1e-5
 
 
 def test_bf16x3_full_size_sampled():
