@@ -122,7 +122,7 @@ static kron_status dispatch(KronDesc& d, cudaStream_t st) {
         if (d.io == KRON_R32F) {   // in-place kernels where they beat the generic one
             if (d.D == 2 && d.N == 16) r = launch_pair16(d, st);
             else if (d.D == 2 && (d.N == 10 || d.N == 14)) r = launch_pair2ip(d, st);
-            else if (d.D == 3 && d.N == 16) r = launch_pair3ip(d, st);
+            else if (d.D == 3 && (d.N == 16 || d.N == 10 || d.N == 14)) r = launch_pair3ip(d, st);
         }
         if (r != KRON_ERR_NOT_SUPPORTED) return r;
         switch (d.io) {

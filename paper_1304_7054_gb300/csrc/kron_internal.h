@@ -82,8 +82,8 @@ kron_status launch_pair16(const KronDesc& d, cudaStream_t s);
 // 2-D n = 10, 14 FP32 pair kernels with the exchange in place (tiles of a
 // multiple of 8 instances); KRON_ERR_NOT_SUPPORTED otherwise.
 kron_status launch_pair2ip(const KronDesc& d, cudaStream_t s);
-// 3-D n = 16 FP32 pair kernel with all contractions in place (one instance per
-// tile); KRON_ERR_NOT_SUPPORTED otherwise.
+// 3-D FP32 pair kernels with all contractions in place (n = 16: one instance
+// per tile; n = 10, 14: four); KRON_ERR_NOT_SUPPORTED otherwise.
 kron_status launch_pair3ip(const KronDesc& d, cudaStream_t s);
 
 // Batched GEMM with a varying first factor (TGEMM_A), after validation; the 1-D
