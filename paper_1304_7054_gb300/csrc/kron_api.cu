@@ -133,6 +133,10 @@ static kron_status dispatch(KronDesc& d, cudaStream_t st) {
         }
         if (r != KRON_ERR_NOT_SUPPORTED) return r;
     }
+    if (d.D == 3 && (d.N & 1) && d.N >= 3 && d.io == KRON_R32F && d.contiguous && d.ycontig) {
+        const kron_status r = launch_fiber3ip(d, st);   // odd n, all contractions in place
+        if (r != KRON_ERR_NOT_SUPPORTED) return r;
+    }
     switch (d.io) {
         case KRON_R32F: return d.D == 2 ? launch_fiber_f32_d2(d, st) : launch_fiber_f32_d3(d, st);
         case KRON_R64F: return d.D == 2 ? launch_fiber_f64_d2(d, st) : launch_fiber_f64_d3(d, st);
