@@ -445,8 +445,8 @@ def kernel_of(kind, n, io, compute):
         return "pair3ip_kernel<f32,n=16,3-D>"
     if kind == 3 and n in (10, 14) and io == "f32":
         return f"pair3pk_kernel<f32,n={n},3-D>"
-    if kind == 3 and n % 2 == 1 and n >= 3 and io == "f32":
-        return f"fiber3ip_kernel<f32,n={n},3-D>"
+    if n % 2 == 1 and n >= 3 and io == "f32":
+        return f"fiberip_kernel<f32,n={n},{kind}-D>"
     if io != "f64" and n % 2 == 0:
         return f"pair_kernel<{io},n={n},{kind}-D>"
     return f"fiber_kernel<{io},n={n},{kind}-D>"

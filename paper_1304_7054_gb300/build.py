@@ -82,7 +82,7 @@ FAMILY_SOURCES = {
     "pair3ip_kernel": ["kron_pair3ip.cu", "kron_pair.cuh", "kron_fiber.cuh", "kron_device.cuh"],
     "pair3pk_kernel": ["kron_pair3ip.cu", "kron_pair.cuh", "kron_fiber.cuh", "kron_device.cuh"],
     "fiber_kernel": ["kron_fiber.cuh", "kron_device.cuh"],
-    "fiber3ip_kernel": ["kron_fiber3ip.cu", "kron_pair.cuh", "kron_fiber.cuh", "kron_device.cuh"],
+    "fiberip_kernel": ["kron_fiberip.cu", "kron_pair.cuh", "kron_fiber.cuh", "kron_device.cuh"],
     "gemm_a_kernel": ["kron_gemm_a.cu", "kron_pair.cuh", "kron_fiber.cuh", "kron_device.cuh"],
     "gemm_a_pair_kernel": ["kron_gemm_a.cu", "kron_pair.cuh", "kron_fiber.cuh", "kron_device.cuh"],
     "kron1_kernel": ["kron_kron1.cu", "kron_pair.cuh", "kron_fiber.cuh", "kron_device.cuh"],

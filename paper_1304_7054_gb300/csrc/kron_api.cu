@@ -133,8 +133,8 @@ static kron_status dispatch(KronDesc& d, cudaStream_t st) {
         }
         if (r != KRON_ERR_NOT_SUPPORTED) return r;
     }
-    if (d.D == 3 && (d.N & 1) && d.N >= 3 && d.io == KRON_R32F && d.contiguous && d.ycontig) {
-        const kron_status r = launch_fiber3ip(d, st);   // odd n, all contractions in place
+    if ((d.N & 1) && d.N >= 3 && d.io == KRON_R32F && d.contiguous && d.ycontig) {
+        const kron_status r = launch_fiberip(d, st);   // odd n, all contractions in place
         if (r != KRON_ERR_NOT_SUPPORTED) return r;
     }
     switch (d.io) {

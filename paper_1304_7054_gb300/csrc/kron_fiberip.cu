@@ -1,4 +1,4 @@
-// 3-D FP32 kernels for odd n with all three mode contractions done in place.
+// 2-D and 3-D FP32 kernels for odd n with all mode contractions done in place.
 //
 // The contractions are those of the other 3-D kernels (Sec. 2.1, the order of
 // Algorithm 1 with the intermediates on chip): mode 3 with M3, mode 2 with M2,
@@ -9,10 +9,10 @@
 // back over the fiber's own words.  So the operand tile is the only on-chip
 // storage, and:
 //
-//   instance q of a tile sits at word n^3 q (packed), element (i, j, k) at
+//   instance q of a tile sits at word n^d q (packed), element (i, j, k) at
 //   i + n j + n^2 k.  Stage A and B threads walk consecutive i (consecutive
 //   words), stage C threads consecutive j (stride n, odd): every scalar shared
-//   access of a warp touches distinct banks.
+//   access of a warp touches distinct banks.  2-D runs stages B and C only.
 //
 // Tiles of P instances (P a multiple of 4, so a tile is a whole number of 16-byte
 // chunks) arrive and leave as one bulk copy (TMA) each; one producer warp streams
@@ -32,7 +32,7 @@ constexpr int kFiMaxRing = 4;
 template <int N>
 struct FiberIpArgs {
     static constexpr int R = (N + 1) / 2;   // output row pairs (last one padded)
-    f2 m3[R * N], m2[R * N], m1[R * N];     // (M[2r, l], M[2r+1, l]) at r + R l
+    f2 m3[R * N], m2[R * N], m1[R * N];     // (M[2r, l], M[2r+1, l]) at r + R l (m3 unused in 2-D)
     const void* X;
     void* Y;
     int64_t batch;
@@ -69,9 +69,10 @@ __device__ __forceinline__ void fiber_in_place(float* p, const f2* Mp) {
     for (int r = 0; r < N; ++r) p[S * r] = (r & 1) ? f2_hi(y[r / 2]) : f2_lo(y[r / 2]);
 }
 
-template <int N>
-__global__ void __launch_bounds__(kFiThreads, 4) fiber3ip_kernel(const __grid_constant__ FiberIpArgs<N> a) {
-    constexpr int NX = N * N * N, NN = N * N;
+template <int N, int D>
+__global__ void __launch_bounds__(kFiThreads, 4) fiberip_kernel(const __grid_constant__ FiberIpArgs<N> a) {
+    constexpr int NN = N * N, NX = D == 3 ? NN * N : NN;
+    constexpr int NF = NX / N;   // fibers per instance and stage
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
     uint64_t* empty = full + kFiMaxRing;
@@ -146,11 +147,13 @@ __global__ void __launch_bounds__(kFiThreads, 4) fiber3ip_kernel(const __grid_co
             for (int e = nbulk + tid; e < nel; e += kFiCompute) buf[e] = X[i0 * NX + e];
             compute_sync_or(false);
         }
-        // Stage A (mode 3): fibers (q, i, j), consecutive threads consecutive i.
+        if constexpr (D == 3) {
+            // Stage A (mode 3): fibers (q, i, j), consecutive threads consecutive i.
 #pragma unroll 1
-        for (int u = tid; u < cnt * NN; u += kFiCompute) {
-            const int q = u / NN, r = u - q * NN;
-            fiber_in_place<N, NN>(buf + q * NX + r, a.m3);
+            for (int u = tid; u < cnt * NN; u += kFiCompute) {
+                const int q = u / NN, r = u - q * NN;
+                fiber_in_place<N, NN>(buf + q * NX + r, a.m3);
+            }
         }
         if (compute_sync_or(!ok)) {
             if (tid == 0)
@@ -159,18 +162,18 @@ __global__ void __launch_bounds__(kFiThreads, 4) fiber3ip_kernel(const __grid_co
                         mbar_wait_bounded(&full[j % NB], (unsigned)(j / NB) & 1u, a.err);
             return;
         }
-        // Stage B (mode 2): fibers (q, i, k).
+        // Stage B (mode 2): fibers (q, i, k) (2-D: (q, i)).
 #pragma unroll 1
-        for (int u = tid; u < cnt * NN; u += kFiCompute) {
-            const int q = u / NN, r = u - q * NN;
+        for (int u = tid; u < cnt * NF; u += kFiCompute) {
+            const int q = u / NF, r = u - q * NF;
             const int i = r % N, k = r / N;
             fiber_in_place<N, N>(buf + q * NX + i + NN * k, a.m2);
         }
         compute_sync_or(false);
         // Stage C (mode 1): fibers (q, j, k) (contiguous), with the epilogue.
 #pragma unroll 1
-        for (int u = tid; u < cnt * NN; u += kFiCompute) {
-            const int q = u / NN, r = u - q * NN;
+        for (int u = tid; u < cnt * NF; u += kFiCompute) {
+            const int q = u / NF, r = u - q * NF;
             float* p = buf + q * NX + N * r;
             float x[N];
 #pragma unroll
@@ -195,11 +198,12 @@ __global__ void __launch_bounds__(kFiThreads, 4) fiber3ip_kernel(const __grid_co
     }
 }
 
-template <int N>
+template <int N, int D>
 kron_status launch_fi_n(const KronDesc& d, cudaStream_t st) {
     constexpr int R = (N + 1) / 2;
+    constexpr int NX = D == 3 ? N * N * N : N * N;
     // instances per tile: about 16-54 KB of operands, a multiple of 4
-    constexpr int P0 = N >= 11 ? 4 : (N >= 9 ? 8 : (N >= 7 ? 16 : (N >= 5 ? 32 : 128)));
+    constexpr int P0 = std::max(4, (6144 / NX) / 4 * 4);
     if (d.P > 0 && d.P % 4) return KRON_ERR_NOT_SUPPORTED;   // other tiles: fiber kernel
     const DeviceInfo& dev = device_info();
     if (dev.sms <= 0) return KRON_ERR_CUDA;
@@ -216,7 +220,7 @@ kron_status launch_fi_n(const KronDesc& d, cudaStream_t st) {
                 out[r + R * l] = (f2)b0 | ((f2)b1 << 32);
             }
     };
-    pairs(d.m3, a.m3);
+    if constexpr (D == 3) pairs(d.m3, a.m3);
     pairs(d.m2, a.m2);
     pairs(d.m1, a.m1);
     a.X = d.X;
@@ -231,12 +235,12 @@ kron_status launch_fi_n(const KronDesc& d, cudaStream_t st) {
     a.P = d.P > 0 ? d.P : P0;
     int nb = d.nstage >= 1 ? d.nstage : 2;   // measured: two buffers at every odd n
     if (nb > kFiMaxRing) nb = kFiMaxRing;
-    auto smem_of = [&](int n_b) { return 128 + (size_t)n_b * a.P * N * N * N * sizeof(float); };
+    auto smem_of = [&](int n_b) { return 128 + (size_t)n_b * a.P * NX * sizeof(float); };
     size_t smem = smem_of(nb);
     while (nb > 1 && smem > dev.smem_per_block_optin) smem = smem_of(--nb);
     if (smem > dev.smem_per_block_optin) return KRON_ERR_NOT_SUPPORTED;
     a.nstage = nb;
-    auto kern = fiber3ip_kernel<N>;
+    auto kern = fiberip_kernel<N, D>;
     if (!ensure_smem_optin((const void*)kern, smem)) return KRON_ERR_CUDA;
     const int64_t ntiles = (d.batch + a.P - 1) / a.P;
     int64_t grid = d.grid;
@@ -253,22 +257,27 @@ kron_status launch_fi_n(const KronDesc& d, cudaStream_t st) {
 
 }  // namespace
 
-// 3-D, odd n >= 3, FP32 storage and arithmetic, contiguous X and Y; tiles that
-// are not a multiple of 4 instances (and other shapes) get KRON_ERR_NOT_SUPPORTED
-// and are left to the fiber kernel.
-kron_status launch_fiber3ip(const KronDesc& d, cudaStream_t st) {
-    if (d.D != 3 || d.io != KRON_R32F || d.comp != KRON_COMPUTE_NATIVE || !d.contiguous || !d.ycontig)
-        return KRON_ERR_NOT_SUPPORTED;
+// Odd n >= 3, 2-D or 3-D, FP32 storage and arithmetic, contiguous X and Y;
+// tiles that are not a multiple of 4 instances (and other shapes) get
+// KRON_ERR_NOT_SUPPORTED and are left to the fiber kernel.
+template <int D>
+kron_status launch_fi_d(const KronDesc& d, cudaStream_t st) {
     switch (d.N) {
-        case 3: return launch_fi_n<3>(d, st);
-        case 5: return launch_fi_n<5>(d, st);
-        case 7: return launch_fi_n<7>(d, st);
-        case 9: return launch_fi_n<9>(d, st);
-        case 11: return launch_fi_n<11>(d, st);
-        case 13: return launch_fi_n<13>(d, st);
-        case 15: return launch_fi_n<15>(d, st);
+        case 3: return launch_fi_n<3, D>(d, st);
+        case 5: return launch_fi_n<5, D>(d, st);
+        case 7: return launch_fi_n<7, D>(d, st);
+        case 9: return launch_fi_n<9, D>(d, st);
+        case 11: return launch_fi_n<11, D>(d, st);
+        case 13: return launch_fi_n<13, D>(d, st);
+        case 15: return launch_fi_n<15, D>(d, st);
         default: return KRON_ERR_NOT_SUPPORTED;
     }
+}
+
+kron_status launch_fiberip(const KronDesc& d, cudaStream_t st) {
+    if (d.io != KRON_R32F || d.comp != KRON_COMPUTE_NATIVE || !d.contiguous || !d.ycontig)
+        return KRON_ERR_NOT_SUPPORTED;
+    return d.D == 3 ? launch_fi_d<3>(d, st) : launch_fi_d<2>(d, st);
 }
 
 }  // namespace kron

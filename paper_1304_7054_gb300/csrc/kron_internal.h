@@ -105,9 +105,9 @@ kron_status launch_gemm_a(const GemmADesc& g, cudaStream_t s);
 // KRON_ERR_NOT_SUPPORTED otherwise.
 kron_status launch_kron1(const GemmADesc& g, cudaStream_t s);
 
-// 3-D odd-n FP32 kernels with all contractions in place (tiles of a multiple of 4
-// instances); KRON_ERR_NOT_SUPPORTED otherwise.
-kron_status launch_fiber3ip(const KronDesc& d, cudaStream_t s);
+// Odd-n FP32 kernels (2-D and 3-D) with all contractions in place (tiles of a
+// multiple of 4 instances); KRON_ERR_NOT_SUPPORTED otherwise.
+kron_status launch_fiberip(const KronDesc& d, cudaStream_t s);
 
 // Tensor-core split-precision kernels (R32F or R16BF storage).
 kron_status launch_tc(const KronDesc& d, cudaStream_t s);

@@ -26,8 +26,9 @@ def test_kernel_names_follow_dispatch():
     assert bench.kernel_of(2, 10, "f32", "native").startswith("pair2ip_kernel")
     assert bench.kernel_of(2, 12, "f32", "native").startswith("pair_kernel")
     assert bench.kernel_of(2, 16, "bf16", "native").startswith("pair_kernel")
-    assert bench.kernel_of(3, 15, "f32", "native").startswith("fiber3ip_kernel")
-    assert bench.kernel_of(2, 15, "f32", "native").startswith("fiber_kernel")
+    assert bench.kernel_of(3, 15, "f32", "native").startswith("fiberip_kernel")
+    assert bench.kernel_of(2, 15, "f32", "native").startswith("fiberip_kernel")
+    assert bench.kernel_of(2, 15, "f64", "native").startswith("fiber_kernel")
     assert bench.kernel_of(3, 16, "f32", "native").startswith("pair3ip_kernel")
     assert bench.kernel_of(3, 10, "f32", "native").startswith("pair3pk_kernel")
     assert bench.kernel_of(2, 16, "f64", "native").startswith("fiber_kernel")

@@ -1,4 +1,4 @@
-"""Parity of the 3-D FP32 kernels for odd n whose three contractions run in
+"""Parity of the 2-D and 3-D FP32 kernels for odd n whose contractions run in
 place (one thread per fiber, tiles of a multiple of 4 packed instances, a ring
 of buffers fed by a producer warp) with the FP64 oracle.
 
@@ -20,16 +20,17 @@ pytestmark = pytest.mark.gpu
 ODD = [3, 5, 7, 9, 11, 13, 15]
 
 
+@pytest.mark.parametrize("kind", [3, 2])
 @pytest.mark.parametrize("n", ODD)
 @pytest.mark.parametrize("P,depth", [(0, 0), (4, 1), (8, 2), (12, 3)])
 @pytest.mark.parametrize("batch", [1, 5, 203, 2001])
-def test_tiles_depths_and_ragged_batches(n, P, depth, batch):
-    b = inputs.make_batch(3, n, batch, seed=800 + n + batch % 53 + P, x_dist="normal")
+def test_tiles_depths_and_ragged_batches(kind, n, P, depth, batch):
+    b = inputs.make_batch(kind, n, batch, seed=800 + n + batch % 53 + P + kind, x_dist="normal")
     try:
-        kg.set_tile_config(3, n, "f32", "native", P, depth)
+        kg.set_tile_config(kind, n, "f32", "native", P, depth)
         Y, X64 = run_gpu(b, guard=64)
     finally:
-        kg.set_tile_config(3, n, "f32", "native", 0, 0)
+        kg.set_tile_config(kind, n, "f32", "native", 0, 0)
     assert max_norm_err(Y, oracle_ref(b, X64), b, X64) <= TOL["f32"]
 
 
@@ -48,16 +49,17 @@ def test_alpha_beta(n, alpha, beta):
     assert float((err / scale).max()) <= TOL["f32"]
 
 
+@pytest.mark.parametrize("kind", [3, 2])
 @pytest.mark.parametrize("n", [7, 15])
-def test_agrees_with_fiber_kernel(n):
-    b = inputs.make_batch(3, n, 301, seed=90 + n, x_dist="normal")
+def test_agrees_with_fiber_kernel(kind, n):
+    b = inputs.make_batch(kind, n, 301, seed=90 + n + kind, x_dist="normal")
     out = []
     for P in (0, 3):
         try:
-            kg.set_tile_config(3, n, "f32", "native", P, 1 if P else 0)
+            kg.set_tile_config(kind, n, "f32", "native", P, 1 if P else 0)
             out.append(run_gpu(b, guard=8))
         finally:
-            kg.set_tile_config(3, n, "f32", "native", 0, 0)
+            kg.set_tile_config(kind, n, "f32", "native", 0, 0)
     for Y, X64 in out:
         assert max_norm_err(Y, oracle_ref(b, X64), b, X64) <= TOL["f32"]
     assert max_norm_err(out[0][0], out[1][0], b, out[0][1]) <= TOL["f32"]
