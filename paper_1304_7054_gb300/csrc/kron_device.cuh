@@ -216,11 +216,4 @@ __device__ __forceinline__ void store_chunks(S* dst, const S (&o)[N]) {
     }
 }
 
-template <typename S, int N>
-__device__ __forceinline__ void store_chunks_f64(double* dst, const double (&o)[N]) {
-#pragma unroll
-    for (int c = 0; c < N / 2; ++c) __stcs(reinterpret_cast<double2*>(dst + 2 * c), make_double2(o[2 * c], o[2 * c + 1]));
-    if constexpr (N % 2) __stcs(dst + N - 1, o[N - 1]);
-}
-
 }  // namespace kron
