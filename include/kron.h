@@ -208,8 +208,16 @@ KRON_API kron_status kron_device_status(kron_stream_t stream);
  * three rounds of ten launches), keeps the fastest in the process-wide table
  * unless it beats the built-in default by less than 2% (then the default, 0 0,
  * is kept), appends the choice to the file named by KRON_TUNE_CACHE (if set;
- * read at first use; later lines override earlier ones), and returns it.  Errors: KRON_ERR_INVALID_VALUE for bad arguments,
- * KRON_ERR_CUDA if a timing call fails.
+ * read at first use; later lines override earlier ones), and returns it.
+ *
+ * For contiguous FP32 batches the tile size also chooses the kernel: the
+ * in-place kernels take their own tile shapes (2-D n = 16: 16 instances; 2-D
+ * n = 10, 14: multiples of 8; 3-D n = 16: 1; 3-D n = 10, 14: 4; odd n: multiples
+ * of 4), and any other tile size runs the generic kernel of that shape.  Every
+ * configuration computes the same result within the documented tolerance.
+ *
+ * Errors: KRON_ERR_INVALID_VALUE for bad arguments, KRON_ERR_CUDA if a timing
+ * call fails.
  */
 KRON_API kron_status kron_set_tile_config(int kind, int n, kron_dtype io, kron_compute comp,
                                           int instances_per_tile, int pipeline_depth);
