@@ -442,6 +442,8 @@ def kernel_of(kind, n, io, compute):
         return f"tc{kind}_kernel<n={n},{io}>"
     if kind == 2 and n == 16 and io == "f32":
         return "pair16_kernel<f32,n=16,2-D>"
+    if kind == 2 and n == 16 and io in ("bf16", "f16"):
+        return f"pair16h_kernel<{io},n=16,2-D>"
     if kind == 2 and n in (10, 14) and io == "f32":
         return f"pair2ip_kernel<f32,n={n},2-D>"
     if kind == 3 and n == 16 and io == "f32":

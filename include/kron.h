@@ -210,8 +210,9 @@ KRON_API kron_status kron_device_status(kron_stream_t stream);
  * is kept), appends the choice to the file named by KRON_TUNE_CACHE (if set;
  * read at first use; later lines override earlier ones), and returns it.
  *
- * For contiguous FP32 batches the tile size also chooses the kernel: the
- * in-place kernels take their own tile shapes (2-D n = 16: 16 instances; 2-D
+ * For contiguous batches the tile size also chooses the kernel: the in-place
+ * kernels take their own tile shapes (2-D n = 16, any storage: 16 instances;
+ * the rest FP32 only: 2-D
  * n = 10, 14: multiples of 8; 3-D n = 16: 1; 3-D n = 10, 14: 4; odd n: multiples
  * of 4), and any other tile size runs the generic kernel of that shape.  Every
  * configuration computes the same result within the documented tolerance.

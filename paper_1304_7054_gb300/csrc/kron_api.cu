@@ -119,9 +119,10 @@ static kron_status dispatch(KronDesc& d, cudaStream_t st) {
     if (d.comp == KRON_COMPUTE_32F_BF16X3) return launch_tc(d, st);
     if (d.contiguous && d.ycontig && d.N % 2 == 0 && d.io != KRON_R64F) {
         kron_status r = KRON_ERR_NOT_SUPPORTED;
-        if (d.io == KRON_R32F) {   // in-place kernels where they beat the generic one
-            if (d.D == 2 && d.N == 16) r = launch_pair16(d, st);
-            else if (d.D == 2 && (d.N == 10 || d.N == 14)) r = launch_pair2ip(d, st);
+        // In-place kernels where they beat the generic one (n = 16 in 2-D for every storage type).
+        if (d.D == 2 && d.N == 16 && d.comp == KRON_COMPUTE_NATIVE) r = launch_pair16(d, st);
+        else if (d.io == KRON_R32F) {
+            if (d.D == 2 && (d.N == 10 || d.N == 14)) r = launch_pair2ip(d, st);
             else if (d.D == 3 && (d.N == 16 || d.N == 10 || d.N == 14)) r = launch_pair3ip(d, st);
         }
         if (r != KRON_ERR_NOT_SUPPORTED) return r;

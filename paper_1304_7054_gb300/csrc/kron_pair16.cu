@@ -186,12 +186,150 @@ __global__ void __launch_bounds__(kThreads, 6) pair16_kernel(const __grid_consta
 
 size_t pair16_smem_bytes(int nb) { return 128 + (size_t)nb * kTileWords * sizeof(float); }
 
+// ---------------------------------------------------------------------------
+// 16-bit storage (bf16, f16), FP32 arithmetic.  W (FP32) cannot overwrite a
+// 16-bit operand, so it has its own buffer -- laid out as the FP32 kernel's
+// tile, conflict-free -- while the results overwrite the dead operand slots
+// and leave by bulk copy.  Operand slot q (two 16-bit elements per 32-bit
+// word) starts at word 136 q + 4 ((q >> 2) & 1): the first stage's 32-bit
+// reads (four instances per warp) and the second stage's 16-byte result
+// writes (eight instances per quarter-warp) touch distinct banks.
+// ---------------------------------------------------------------------------
+constexpr int kHSlotWords = 136;
+constexpr int kHTileBytes = 8704;                // 16 slots, rounded to 128 bytes
+constexpr int kHWBytes = kTileWords * 4;         // W: the FP32 tile layout
+
+__device__ __forceinline__ int hslot_words(int q) { return kHSlotWords * q + 4 * ((q >> 2) & 1); }
+
+template <typename S>
+__global__ void __launch_bounds__(kThreads, 6) pair16h_kernel(const __grid_constant__ PairArgs<kN, 2> a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem);
+    uint64_t* empty = full + kMaxRing;
+    const int NB = a.nstage;
+    unsigned char* ring = smem + 128;
+    float* W = reinterpret_cast<float*>(ring + NB * kHTileBytes);
+    const int tid = threadIdx.x;
+    const int64_t ntiles = (a.batch + kTileP - 1) / kTileP;
+    const int64_t grid = gridDim.x;
+    if (tid == 0) {
+        for (int s = 0; s < NB; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kCompute);
+        }
+        fence_barrier_init();
+    }
+    __syncthreads();
+
+    if (tid >= kCompute) {   // producer: 512-byte bulk copies, one per instance
+        const int lane = tid - kCompute;
+        const uint64_t pol = l2_evict_first_policy();
+        S* Y = static_cast<S*>(a.Y);
+        const S* X = static_cast<const S*>(a.X);
+        auto slot = [&](int s, int q) { return reinterpret_cast<unsigned*>(ring + s * kHTileBytes) + hslot_words(q); };
+        auto store_tile = [&](int s, int64_t t) {
+            const int64_t i0 = t * kTileP;
+            const int c = (int)min((int64_t)kTileP, a.batch - i0);
+            if (lane < c) bulk_s2g(Y + (i0 + lane) * kNX, slot(s, lane), kNX * 2u);
+            bulk_commit();
+        };
+        int it = 0;
+        for (int64_t tile = blockIdx.x; tile < ntiles; tile += grid, ++it) {
+            const int s = it % NB;
+            if (it >= NB) {
+                if (!mbar_wait_bounded(&empty[s], (unsigned)(it / NB - 1) & 1u, a.err)) {
+                    bulk_wait_all();
+                    return;
+                }
+                store_tile(s, tile - (int64_t)NB * grid);
+                bulk_wait_read();
+            }
+            const int64_t inst0 = tile * kTileP;
+            const int cnt = (int)min((int64_t)kTileP, a.batch - inst0);
+            fence_proxy_async_smem();
+            if (lane == 0) mbar_arrive_expect_tx(&full[s], (unsigned)cnt * kNX * 2u);
+            __syncwarp();
+            if (lane < cnt) bulk_g2s(slot(s, lane), X + (inst0 + lane) * kNX, kNX * 2u, &full[s], pol);
+        }
+        for (int j = it > NB ? it - NB : 0; j < it; ++j) {
+            if (!mbar_wait_bounded(&empty[j % NB], (unsigned)(j / NB) & 1u, a.err)) break;
+            store_tile(j % NB, blockIdx.x + (int64_t)j * grid);
+        }
+        bulk_wait_all();
+        return;
+    }
+
+    const f2* m1p = reinterpret_cast<const f2*>(a.m1);
+    const S* Yg = static_cast<const S*>(a.Y);
+    int it = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += grid, ++it) {
+        const int s = it % NB;
+        unsigned* tw = reinterpret_cast<unsigned*>(ring + s * kHTileBytes);
+        const int64_t inst0 = tile * kTileP;
+        const int cnt = (int)min((int64_t)kTileP, a.batch - inst0);
+        const bool ok = mbar_wait_bounded(&full[s], (unsigned)(it / NB) & 1u, a.err);
+        compute_sync_or(false);   // the previous tile's second stage has read W
+        // Stage 1: rows (l, l+1) of instance q (one 32-bit word per column) times M2^T.
+        {
+            const int q = tid >> 3, l = 2 * (tid & 7);
+            if (q < cnt) {
+                const S* xq = reinterpret_cast<const S*>(tw + hslot_words(q)) + l;
+                f2 x[kN], w[kN];
+#pragma unroll
+                for (int m = 0; m < kN; ++m) x[m] = load_pair<S>(xq + kN * m);
+                contract_dup<kN>(a.da, x, w);
+                float* wq = W + slot_of(q) + l;
+#pragma unroll
+                for (int j = 0; j < kN; ++j) *reinterpret_cast<f2*>(wq + kN * j) = w[j];
+            }
+        }
+        if (compute_sync_or(!ok)) {
+            if (tid == 0)
+                for (int j = it; j < it + NB; ++j)
+                    if (blockIdx.x + (int64_t)j * grid < ntiles)
+                        mbar_wait_bounded(&full[j % NB], (unsigned)(j / NB) & 1u, a.err);
+            return;
+        }
+        // Stage 2: column j of W times M1; the 16-bit results go over the operand slot.
+        const int q = tid & 15, j0 = tid >> 4;
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+            const int j = j0 + 8 * h;
+            if (q >= cnt) continue;
+            float w[kN];
+            load_col(W + slot_of(q) + kN * j, w);
+            f2 y[kN / 2];
+            contract_rows<kN>(m1p, w, y);
+            if (!a.alpha_one) {
+                const f2 al = f2_pack(a.alpha, a.alpha);
+#pragma unroll
+                for (int r = 0; r < kN / 2; ++r) y[r] = fmul2(y[r], al);
+            }
+            if (!a.beta_zero) {
+                const S* yg = Yg + (inst0 + q) * kNX + kN * j;
+                const f2 be = f2_pack(a.beta, a.beta);
+#pragma unroll
+                for (int r = 0; r < kN / 2; ++r) y[r] = ffma2(be, load_pair<S>(yg + 2 * r), y[r]);
+            }
+            unsigned* yw = tw + hslot_words(q) + (kN / 2) * j;
+#pragma unroll
+            for (int c = 0; c < kN / 8; ++c)
+                *reinterpret_cast<uint4*>(yw + 4 * c) = make_uint4(pack16<S>(y[4 * c]), pack16<S>(y[4 * c + 1]),
+                                                                   pack16<S>(y[4 * c + 2]), pack16<S>(y[4 * c + 3]));
+        }
+        fence_proxy_async_smem();
+        mbar_arrive(&empty[s]);
+    }
+}
+
+size_t pair16h_smem_bytes(int nb) { return 128 + (size_t)nb * kHTileBytes + kHWBytes; }
+
 }  // namespace
 
-// 2-D, n = 16, FP32 storage and arithmetic, contiguous X and Y.  Tile sizes
-// other than 16 instances are left to the generic pair kernel.
+// 2-D, n = 16, FP32 arithmetic on FP32, bf16 or f16 storage, contiguous X and Y.
+// Tile sizes other than 16 instances are left to the generic pair kernel.
 kron_status launch_pair16(const KronDesc& d, cudaStream_t st) {
-    if (d.D != 2 || d.N != kN || d.io != KRON_R32F || d.comp != KRON_COMPUTE_NATIVE || !d.contiguous ||
+    if (d.D != 2 || d.N != kN || d.io == KRON_R64F || d.comp != KRON_COMPUTE_NATIVE || !d.contiguous ||
         !d.ycontig || (d.P > 0 && d.P != kTileP))
         return KRON_ERR_NOT_SUPPORTED;
     const DeviceInfo& dev = device_info();
@@ -218,15 +356,20 @@ kron_status launch_pair16(const KronDesc& d, cudaStream_t st) {
     a.err = device_error_word();
     if (!a.err) return KRON_ERR_CUDA;
     a.P = kTileP;
-    // One buffer per CTA (measured best: the six to seven resident CTAs per SM
-    // overlap one another's copies; a second buffer costs resident CTAs).
-    int nb = d.nstage >= 1 ? d.nstage : 1;
+    // FP32: one buffer per CTA (measured best: the six to seven resident CTAs
+    // per SM overlap one another's copies; a second buffer costs resident CTAs).
+    // 16-bit: two (the tiles are half the size; measured 8 % faster than one).
+    const bool h = d.io != KRON_R32F;
+    int nb = d.nstage >= 1 ? d.nstage : (h ? 2 : 1);
     if (nb > kMaxRing) nb = kMaxRing;
-    size_t smem = pair16_smem_bytes(nb);
-    while (nb > 1 && smem > dev.smem_per_block_optin) smem = pair16_smem_bytes(--nb);
+    auto smem_of = [&](int n_b) { return h ? pair16h_smem_bytes(n_b) : pair16_smem_bytes(n_b); };
+    size_t smem = smem_of(nb);
+    while (nb > 1 && smem > dev.smem_per_block_optin) smem = smem_of(--nb);
     if (smem > dev.smem_per_block_optin) return KRON_ERR_NOT_SUPPORTED;
     a.nstage = nb;
-    const void* kern = (const void*)pair16_kernel;
+    const void* kern = !h ? (const void*)pair16_kernel
+                          : (d.io == KRON_R16BF ? (const void*)pair16h_kernel<__nv_bfloat16>
+                                                : (const void*)pair16h_kernel<__half>);
     if (!ensure_smem_optin(kern, smem)) return KRON_ERR_CUDA;
     const int64_t ntiles = (d.batch + kTileP - 1) / kTileP;
     int64_t grid = d.grid;
