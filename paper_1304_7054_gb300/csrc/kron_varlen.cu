@@ -13,11 +13,15 @@
 // (M[i,l], M[i+1,l]) and the operand duplicated), so each stage writes its
 // outputs as adjacent pairs; rows are padded to an even count.
 //
-// Data flow per CTA: the operand elements of the next tile are loaded into
-// registers (any alignment, coalesced) while the current tile is contracted in
-// shared memory; the last contraction writes its fibers into the operand buffer
-// (dead after the first contraction), from which consecutive threads copy the
-// outputs to Y (coalesced); then the next tile is committed to that buffer.
+// Data flow per CTA: two operand buffers.  While one tile is contracted, the
+// next one arrives in the other buffer by bulk copies, one per instance: an
+// instance starts anywhere (4-byte alignment for FP32), so each copy takes the
+// 16-byte-aligned span around it and the instance sits at its alignment phase
+// inside a 16-byte-aligned slot.  The last contraction writes each instance
+// contiguously into its slot (dead after the first contraction) at the phase of
+// its place in Y; the 16-byte-aligned middle leaves by one bulk copy and the at
+// most three elements on either side by plain stores.  Global memory is thus
+// read and written in whole aligned granules, with no per-element address work.
 //
 // Workspace (caller-owned device memory, written on the first execute with a
 // given pointer): tile table (int4: class key, first sorted index, count, 0),
@@ -37,8 +41,7 @@
 namespace kron {
 
 constexpr int kVlThreads = 256;
-constexpr int kVlRegs = 16;                            // prefetched elements per thread
-constexpr int kVlMaxTile = kVlThreads * kVlRegs;       // elements per tile
+constexpr int kVlMaxTile = 4096;                       // operand elements per tile
 constexpr int kVlKeys = 32;                            // class key = 16 (kind - 2) + n - 1
 
 __host__ __device__ constexpr int sq_sum(int n) { return (n - 1) * n * (2 * n - 1) / 6; }   // sum k^2, k < n
@@ -82,32 +85,69 @@ __device__ __forceinline__ int vl_nx(int key) {
     return key < 16 ? n * n : n * n * n;
 }
 
-// Loads the operand elements of tile `td` into registers (element e = tid +
-// kVlThreads * r); xo[q] is the X offset of the tile's instance q (shared memory).
+// Slot of one instance in an operand buffer: its elements plus up to 15 bytes
+// of alignment phase, rounded to 16 bytes.
+__host__ __device__ constexpr int vl_slot_bytes(int nx, int es) { return (nx * es + 15 + 15) / 16 * 16; }
+
+// Alignment phase (in elements) of element offset `off` of an array at `base`.
 template <typename S>
-__device__ __forceinline__ void vl_prefetch(const VarlenArgs& a, int4 td, const int* xo, S (&v)[kVlRegs]) {
+__device__ __forceinline__ int vl_phase(const void* base, int off) {
+    return (int)((((unsigned)(uintptr_t)base) + (unsigned)off * (unsigned)sizeof(S)) & 15u) / (int)sizeof(S);
+}
+
+// Issued by warp 0: one bulk copy per instance of tile `td` (X offsets xo[]) into
+// the slots of buffer `xt`, completing on `bar`.  Each copy covers the aligned
+// 16-byte granules that hold the instance.
+template <typename S>
+__device__ __forceinline__ void vl_issue_loads(const VarlenArgs& a, int4 td, const int* xo, unsigned char* xt,
+                                               uint64_t* bar, uint64_t pol) {
+    const int lane = threadIdx.x & 31;
     const int nx = vl_nx(td.x);
-    const unsigned inv = a.cls[td.x].inv;
-    const int total = td.z * nx;
-    const S* X = static_cast<const S*>(a.X);
+    const int slot = vl_slot_bytes(nx, (int)sizeof(S));
+    unsigned bytes = 0;
+    for (int q = lane; q < td.z; q += 32) {
+        const unsigned ph = (((unsigned)(uintptr_t)a.X) + (unsigned)xo[q] * (unsigned)sizeof(S)) & 15u;
+        bytes += (ph + (unsigned)nx * (unsigned)sizeof(S) + 15u) & ~15u;
+    }
 #pragma unroll
-    for (int r = 0; r < kVlRegs; ++r) {
-        const int e = threadIdx.x + kVlThreads * r;
-        if (e < total) {
-            const int q = nx == 1 ? e : (int)__umulhi((unsigned)e, inv);
-            v[r] = X[(int64_t)xo[q] + (e - q * nx)];
-        }
+    for (int o = 16; o > 0; o >>= 1) bytes += __shfl_xor_sync(0xffffffffu, bytes, o);
+    fence_proxy_async_smem();
+    if (lane == 0) mbar_arrive_expect_tx(bar, bytes);
+    __syncwarp();
+    for (int q = lane; q < td.z; q += 32) {
+        const uintptr_t src = (uintptr_t)(static_cast<const S*>(a.X) + xo[q]);
+        const unsigned ph = (unsigned)(src & 15u);
+        bulk_g2s(xt + q * slot, (const void*)(src - ph), (ph + (unsigned)nx * (unsigned)sizeof(S) + 15u) & ~15u, bar,
+                 pol);
     }
 }
 
+// Issued by warp 0 after the last contraction: per instance, the aligned middle
+// of its run in Y by one bulk copy, the partial granules at both ends by plain
+// stores.  The slot holds the instance at its phase in Y, so slot and Y agree
+// modulo 16 bytes.
 template <typename S>
-__device__ __forceinline__ void vl_commit(int4 td, const S (&v)[kVlRegs], S* xt) {
-    const int total = td.z * vl_nx(td.x);
-#pragma unroll
-    for (int r = 0; r < kVlRegs; ++r) {
-        const int e = threadIdx.x + kVlThreads * r;
-        if (e < total) xt[e] = v[r];
+__device__ __forceinline__ void vl_issue_stores(const VarlenArgs& a, int4 td, const int* yo, const unsigned char* xt) {
+    const int lane = threadIdx.x & 31;
+    const int nx = vl_nx(td.x);
+    const int slot = vl_slot_bytes(nx, (int)sizeof(S));
+    for (int q = lane; q < td.z; q += 32) {
+        S* dst = static_cast<S*>(a.Y) + yo[q];
+        const unsigned ph = (unsigned)((uintptr_t)dst & 15u);
+        const S* src = reinterpret_cast<const S*>(xt + q * slot + ph);
+        const unsigned total = (unsigned)nx * (unsigned)sizeof(S);
+        const unsigned head = ph ? 16u - ph : 0u;
+        if (head >= total) {   // the whole instance inside one granule
+            for (int e = 0; e < nx; ++e) dst[e] = src[e];
+            continue;
+        }
+        const unsigned mid = (total - head) & ~15u;
+        for (unsigned e = 0; e < head / sizeof(S); ++e) dst[e] = src[e];
+        if (mid) bulk_s2g(reinterpret_cast<unsigned char*>(dst) + head,
+                          reinterpret_cast<const unsigned char*>(src) + head, mid);
+        for (unsigned e = (head + mid) / sizeof(S); e < (unsigned)nx; ++e) dst[e] = src[e];
     }
+    bulk_commit();
 }
 
 // Packed-pair contraction of one fiber: (y[2r], y[2r+1]) = M[2r:2r+2, :] x, with
@@ -134,43 +174,58 @@ __device__ __forceinline__ void vl_store_pairs(float* dst, const f2 (&y)[vl_rows
     for (int r = 0; r < vl_rows(N) / 2; ++r) *reinterpret_cast<f2*>(dst + 2 * r) = y[r];
 }
 
-// Output pairs rounded to the storage type, staged at dst[2r].
+// Output fiber of N elements at dst[0..N) (contiguous): pairs (rows 2r, 2r+1)
+// rounded to the storage type and stored as one word where dst is aligned for
+// it, else element by element (the padding row of an odd N is dropped).
 template <typename S, int N>
 __device__ __forceinline__ void vl_stage_out(S* dst, const f2 (&y)[vl_rows(N) / 2]) {
-    if constexpr (sizeof(S) == 4) {
+    const bool paired = ((uintptr_t)dst & (2 * sizeof(S) - 1)) == 0;
+    if (paired) {
 #pragma unroll
-        for (int r = 0; r < vl_rows(N) / 2; ++r) *reinterpret_cast<f2*>(dst + 2 * r) = y[r];
+        for (int r = 0; r < N / 2; ++r) {
+            if constexpr (sizeof(S) == 4)
+                *reinterpret_cast<f2*>(dst + 2 * r) = y[r];
+            else
+                *reinterpret_cast<unsigned*>(dst + 2 * r) = pack16<S>(y[r]);
+        }
     } else {
 #pragma unroll
-        for (int r = 0; r < vl_rows(N) / 2; ++r) *reinterpret_cast<unsigned*>(dst + 2 * r) = pack16<S>(y[r]);
+        for (int r = 0; r < N / 2; ++r) {
+            dst[2 * r] = store_cvt<S, float>(f2_lo(y[r]));
+            dst[2 * r + 1] = store_cvt<S, float>(f2_hi(y[r]));
+        }
     }
+    if constexpr (N & 1) dst[N - 1] = store_cvt<S, float>(f2_lo(y[N / 2]));
 }
 
-// One tile of class (D, N).  Operand tile xt: instance-major, column-major inside
-// (linear).  Exchange layouts put each stage's output pairs next to each other:
+// One tile of class (D, N) in buffer xt: instance q's operands at slot q, phase
+// vl_phase(X, xo[q]); its outputs go to the same slot at phase vl_phase(Y, yo[q]),
+// contiguous and column-major.  Exchange layouts put each stage's output pairs
+// next to each other:
 //   2-D   W(l, j)    at j + KP l                 (stage 1 writes pairs along j)
 //   3-D   T(i, j, k) at k + KP i + KP N j        (stage A: pairs along k)
 //         U(i, j, k) at j + KP k + KP N i        (stage B: pairs along j)
-//   out   Y(i, j, k) at i + KP (j + N k)         (last stage: pairs along i)
-// The outputs are staged in the other operand buffer `ot` and copied to Y by
-// consecutive threads.
+// and the last stage writes pairs along i.
 template <typename S, int N, int D>
-__device__ __forceinline__ void vl_tile(const VarlenArgs& a, int4 td, S* xt, S* ot, float* ex1, float* ex2,
-                                        const int* yo) {
+__device__ __forceinline__ void vl_tile(const VarlenArgs& a, int4 td, unsigned char* xt, float* ex1, float* ex2,
+                                        const int* xo, const int* yo) {
     constexpr int NX = ipow(N, D);
     constexpr int KP = vl_kp(N);
     constexpr int R = vl_rows(N) / 2;
-    constexpr int EXQ = KP * ipow(N, D - 1);   // exchange / staging elements per instance
+    constexpr int EXQ = KP * ipow(N, D - 1);   // exchange elements per instance
+    constexpr int SLOT = vl_slot_bytes(NX, (int)sizeof(S));
     const float* m1 = a.coef + vl_slot(D, N);
     const float* m2 = m1 + vl_rows(N) * N;
     const float* m3 = m2 + vl_rows(N) * N;
     const int cnt = td.z;
     const int tid = threadIdx.x;
+    const void* X = a.X;
+    const void* Y = a.Y;
     if constexpr (D == 2) {
         const int F = cnt * N;
         for (int f = tid; f < F; f += kVlThreads) {   // stage 1: mode 2, fibers (l, q)
             const int q = f / N, l = f - q * N;
-            const S* xr = xt + q * NX + l;
+            const S* xr = reinterpret_cast<const S*>(xt + q * SLOT) + vl_phase<S>(X, xo[q]) + l;
             float x[N];
 #pragma unroll
             for (int m = 0; m < N; ++m) x[m] = load_cvt<float, S>(xr[N * m]);
@@ -187,14 +242,14 @@ __device__ __forceinline__ void vl_tile(const VarlenArgs& a, int4 td, S* xt, S* 
             for (int l = 0; l < N; ++l) w[l] = wr[KP * l];
             f2 y[R];
             vl_contract<N>(m1, w, y);
-            vl_stage_out<S, N>(ot + q * EXQ + KP * j, y);
+            vl_stage_out<S, N>(reinterpret_cast<S*>(xt + q * SLOT) + vl_phase<S>(Y, yo[q]) + N * j, y);
         }
     } else {
         const int F = cnt * N * N;
         for (int f = tid; f < F; f += kVlThreads) {   // stage A: mode 3, fibers (i, j)
             const int q = f / (N * N), r = f - q * (N * N);
             const int i = r % N, j = r / N;
-            const S* xr = xt + q * NX + i + N * j;
+            const S* xr = reinterpret_cast<const S*>(xt + q * SLOT) + vl_phase<S>(X, xo[q]) + i + N * j;
             float x[N];
 #pragma unroll
             for (int p = 0; p < N; ++p) x[p] = load_cvt<float, S>(xr[N * N * p]);
@@ -224,63 +279,55 @@ __device__ __forceinline__ void vl_tile(const VarlenArgs& a, int4 td, S* xt, S* 
             for (int l = 0; l < N; ++l) u[l] = ur[KP * N * l];
             f2 y[R];
             vl_contract<N>(m1, u, y);
-            vl_stage_out<S, N>(ot + q * EXQ + KP * (j + N * k), y);
+            vl_stage_out<S, N>(reinterpret_cast<S*>(xt + q * SLOT) + vl_phase<S>(Y, yo[q]) + N * (j + N * k), y);
         }
-    }
-    __syncthreads();
-    // coalesced copy of the finished instances to Y
-    S* Y = static_cast<S*>(a.Y);
-    const unsigned inv = a.cls[td.x].inv;
-    for (int e = tid; e < cnt * NX; e += kVlThreads) {
-        const int q = NX == 1 ? e : (int)__umulhi((unsigned)e, inv);
-        const int r = e - q * NX;
-        Y[(int64_t)yo[q] + r] = ot[q * EXQ + KP * (r / N) + r % N];
     }
 }
 
 template <typename S, int D>
-__device__ __forceinline__ void vl_dispatch_n(const VarlenArgs& a, int4 td, S* xt, S* ot, float* ex1, float* ex2,
-                                              const int* yo) {
+__device__ __forceinline__ void vl_dispatch_n(const VarlenArgs& a, int4 td, unsigned char* xt, float* ex1, float* ex2,
+                                              const int* xo, const int* yo) {
     switch ((td.x & 15) + 1) {
-        case 1: vl_tile<S, 1, D>(a, td, xt, ot, ex1, ex2, yo); break;
-        case 2: vl_tile<S, 2, D>(a, td, xt, ot, ex1, ex2, yo); break;
-        case 3: vl_tile<S, 3, D>(a, td, xt, ot, ex1, ex2, yo); break;
-        case 4: vl_tile<S, 4, D>(a, td, xt, ot, ex1, ex2, yo); break;
-        case 5: vl_tile<S, 5, D>(a, td, xt, ot, ex1, ex2, yo); break;
-        case 6: vl_tile<S, 6, D>(a, td, xt, ot, ex1, ex2, yo); break;
-        case 7: vl_tile<S, 7, D>(a, td, xt, ot, ex1, ex2, yo); break;
-        case 8: vl_tile<S, 8, D>(a, td, xt, ot, ex1, ex2, yo); break;
-        case 9: vl_tile<S, 9, D>(a, td, xt, ot, ex1, ex2, yo); break;
-        case 10: vl_tile<S, 10, D>(a, td, xt, ot, ex1, ex2, yo); break;
-        case 11: vl_tile<S, 11, D>(a, td, xt, ot, ex1, ex2, yo); break;
-        case 12: vl_tile<S, 12, D>(a, td, xt, ot, ex1, ex2, yo); break;
-        case 13: vl_tile<S, 13, D>(a, td, xt, ot, ex1, ex2, yo); break;
-        case 14: vl_tile<S, 14, D>(a, td, xt, ot, ex1, ex2, yo); break;
-        case 15: vl_tile<S, 15, D>(a, td, xt, ot, ex1, ex2, yo); break;
-        case 16: vl_tile<S, 16, D>(a, td, xt, ot, ex1, ex2, yo); break;
+        case 1: vl_tile<S, 1, D>(a, td, xt, ex1, ex2, xo, yo); break;
+        case 2: vl_tile<S, 2, D>(a, td, xt, ex1, ex2, xo, yo); break;
+        case 3: vl_tile<S, 3, D>(a, td, xt, ex1, ex2, xo, yo); break;
+        case 4: vl_tile<S, 4, D>(a, td, xt, ex1, ex2, xo, yo); break;
+        case 5: vl_tile<S, 5, D>(a, td, xt, ex1, ex2, xo, yo); break;
+        case 6: vl_tile<S, 6, D>(a, td, xt, ex1, ex2, xo, yo); break;
+        case 7: vl_tile<S, 7, D>(a, td, xt, ex1, ex2, xo, yo); break;
+        case 8: vl_tile<S, 8, D>(a, td, xt, ex1, ex2, xo, yo); break;
+        case 9: vl_tile<S, 9, D>(a, td, xt, ex1, ex2, xo, yo); break;
+        case 10: vl_tile<S, 10, D>(a, td, xt, ex1, ex2, xo, yo); break;
+        case 11: vl_tile<S, 11, D>(a, td, xt, ex1, ex2, xo, yo); break;
+        case 12: vl_tile<S, 12, D>(a, td, xt, ex1, ex2, xo, yo); break;
+        case 13: vl_tile<S, 13, D>(a, td, xt, ex1, ex2, xo, yo); break;
+        case 14: vl_tile<S, 14, D>(a, td, xt, ex1, ex2, xo, yo); break;
+        case 15: vl_tile<S, 15, D>(a, td, xt, ex1, ex2, xo, yo); break;
+        case 16: vl_tile<S, 16, D>(a, td, xt, ex1, ex2, xo, yo); break;
     }
 }
 
 template <typename S>
-__global__ void __launch_bounds__(kVlThreads) varlen_kernel(const __grid_constant__ VarlenArgs a, int xbuf_elems) {
+__global__ void __launch_bounds__(kVlThreads) varlen_kernel(const __grid_constant__ VarlenArgs a, int xbuf_bytes) {
     extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem);   // one barrier per operand buffer
     // Offsets of the instances of three consecutive tiles of this CTA (a ring):
     // X offsets then Y offsets, kVlThreads each (a tile has at most that many).
-    int* ring = reinterpret_cast<int*>(smem);
-    // One operand buffer: it is dead after the first contraction, so the last
-    // contraction stages the outputs in it, and the next tile (held in registers
-    // meanwhile) is committed into it after the copy-out.
-    S* xb = reinterpret_cast<S*>(smem + 6 * kVlThreads * sizeof(int));
-    float* ex1 = reinterpret_cast<float*>(
-        smem + round_up(6 * kVlThreads * sizeof(int) + (size_t)xbuf_elems * sizeof(S), 128));
+    int* ring = reinterpret_cast<int*>(smem + 128);
+    unsigned char* xbuf = smem + 128 + 6 * kVlThreads * sizeof(int);
+    float* ex1 = reinterpret_cast<float*>(xbuf + 2 * xbuf_bytes);
     const int G = gridDim.x;
     const int tid = threadIdx.x;
     const int t0 = blockIdx.x;
     if (t0 >= a.ntiles) return;
     const int4 none = make_int4(0, 0, 0, 0);
+    if (tid == 0) {
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        fence_barrier_init();
+    }
     // Pipeline: descriptors are read two tiles ahead, instance offsets one tile
-    // ahead (through the ring), operand elements one tile ahead (registers), so no
-    // global load is waited for at the start of a tile.
+    // ahead (through the ring), operands one tile ahead (the other buffer).
     int4 d0 = a.tiles[t0];
     int4 d1 = t0 + G < a.ntiles ? a.tiles[t0 + G] : none;
     int4 d2 = t0 + 2 * G < a.ntiles ? a.tiles[t0 + 2 * G] : none;
@@ -293,12 +340,10 @@ __global__ void __launch_bounds__(kVlThreads) varlen_kernel(const __grid_constan
         ring[3 * kVlThreads + tid] = (int)a.yoff[d1.y + tid];
     }
     __syncthreads();
-    S v[kVlRegs];
-    vl_prefetch<S>(a, d0, ring, v);
-    vl_commit<S>(d0, v, xb);
-    __syncthreads();
+    const uint64_t pol = l2_evict_first_policy();
     int it = 0;
     for (int tile = t0; tile < a.ntiles; ++it, tile += G) {
+        const int b = it & 1;
         const int s0 = it % 3, s1 = (it + 1) % 3, s2 = (it + 2) % 3;
         // offsets of tile + 2G, stored at the end of this tile
         int xo2 = 0, yo2 = 0;
@@ -307,19 +352,45 @@ __global__ void __launch_bounds__(kVlThreads) varlen_kernel(const __grid_constan
             yo2 = (int)a.yoff[d2.y + tid];
         }
         const int4 d3 = tile + 3 * G < a.ntiles ? a.tiles[tile + 3 * G] : none;
-        if (d1.z) vl_prefetch<S>(a, d1, ring + 2 * kVlThreads * s1, v);
+        if (tid < 32) {
+            // Operands of this tile (first iteration only) and of the next one; the
+            // other buffer's last results have left shared memory before it is reused.
+            for (int u = it == 0 ? 0 : 1; u < 2; ++u) {
+                const int4 du = u ? d1 : d0;
+                if (!du.z) break;
+                if (u) {
+                    bulk_wait_read();
+                    __syncwarp();
+                }
+                vl_issue_loads<S>(a, du, ring + 2 * kVlThreads * (u ? s1 : s0), xbuf + (b ^ u) * xbuf_bytes,
+                                  &full[b ^ u], pol);
+            }
+        }
+        const bool ok = mbar_wait_bounded(&full[b], (unsigned)(it >> 1) & 1u, a.err);
+        if (__syncthreads_or(!ok)) {
+            // wait (bounded) for copies still in flight into this CTA's buffers
+            if (tid == 0) {
+                mbar_wait_bounded(&full[b], (unsigned)(it >> 1) & 1u, a.err);
+                if (d1.z) mbar_wait_bounded(&full[b ^ 1], (unsigned)((it + 1) >> 1) & 1u, a.err);
+            }
+            if (tid < 32) bulk_wait_all();
+            return;
+        }
         const int key = d0.x;
         const int P = a.cls[key].P;
         const int n = (key & 15) + 1;
         // exchange buffer 2 starts after P * (per-instance size of buffer 1)
         float* ex2 = ex1 + (size_t)P * vl_kp(n) * (key < 16 ? n : n * n);
-        const int* yo = ring + 2 * kVlThreads * s0 + kVlThreads;
+        unsigned char* xt = xbuf + b * xbuf_bytes;
+        const int* xo = ring + 2 * kVlThreads * s0;
+        const int* yo = xo + kVlThreads;
         if (key < 16)
-            vl_dispatch_n<S, 2>(a, d0, xb, xb, ex1, ex2, yo);
+            vl_dispatch_n<S, 2>(a, d0, xt, ex1, ex2, xo, yo);
         else
-            vl_dispatch_n<S, 3>(a, d0, xb, xb, ex1, ex2, yo);
-        __syncthreads();   // outputs copied out before the next tile lands in xb
-        if (d1.z) vl_commit<S>(d1, v, xb);
+            vl_dispatch_n<S, 3>(a, d0, xt, ex1, ex2, xo, yo);
+        fence_proxy_async_smem();   // results visible to the bulk copies
+        __syncthreads();
+        if (tid < 32) vl_issue_stores<S>(a, d0, yo, xt);
         if (tid < d2.z) {
             ring[2 * kVlThreads * s2 + tid] = xo2;
             ring[2 * kVlThreads * s2 + kVlThreads + tid] = yo2;
@@ -329,6 +400,7 @@ __global__ void __launch_bounds__(kVlThreads) varlen_kernel(const __grid_constan
         d1 = d2;
         d2 = d3;
     }
+    if (tid < 32) bulk_wait_all();
 }
 
 // ---------------------------------------------------------------------------
@@ -363,7 +435,7 @@ struct kron_varlen_plan {
     std::vector<int4> tiles;
     size_t ws_bytes = 0;
     size_t smem = 0;
-    int xbuf_elems = 0;
+    int xbuf_bytes = 0;                        // one operand buffer (two per CTA)
     int grid = 0;
     kron::VarlenArgs* args = nullptr;          // heap: ~30 KB
     // graph state
@@ -414,14 +486,14 @@ static kron_status vl_build(kron_varlen_plan* p) {
             const int c = (int)std::min<int64_t>(P, cnt - s);
             tl.push_back(T{flops * c, make_int4(key, (int)(start + s), c, 0)});
         }
-        max_x = std::max(max_x, (size_t)P * std::max(nx, (nx / n) * vl_kp(n)));   // operands / padded outputs
+        max_x = std::max(max_x, (size_t)P * vl_slot_bytes(nx, (int)es));
         max_smem_rest = std::max(max_smem_rest, vl_ex_floats(kind, n, P) * sizeof(float));
     }
     if (p->order.size() > (size_t)INT32_MAX) return KRON_ERR_NOT_SUPPORTED;
     std::stable_sort(tl.begin(), tl.end(), [](const T& a, const T& b) { return a.work > b.work; });
     for (const T& t : tl) p->tiles.push_back(t.td);
-    p->xbuf_elems = (int)round_up(max_x, 64);
-    p->smem = round_up(6 * kVlThreads * sizeof(int) + (size_t)p->xbuf_elems * es, 128) + max_smem_rest;
+    p->xbuf_bytes = (int)round_up(max_x, 128);
+    p->smem = 128 + 6 * kVlThreads * sizeof(int) + 2 * (size_t)p->xbuf_bytes + max_smem_rest;
     // Sized for one tile per instance (the most any tile size can give), so that
     // re-tuning never outgrows a workspace sized before it.
     p->ws_bytes = round_up(p->order.size() * sizeof(int4), 256) + 2 * round_up(p->order.size() * 8, 256);
@@ -492,7 +564,7 @@ static kron_status vl_launch(kron_varlen_plan* p, const void* X, void* Y, void* 
         return KRON_ERR_CUDA;
     int grid = std::max(1, per_sm) * dev.sms;
     grid = (int)std::min<size_t>((size_t)grid, p->tiles.size());
-    int xbe = p->xbuf_elems;
+    int xbe = p->xbuf_bytes;
     void* kargs[2] = {p->args, &xbe};
     cudaKernelNodeParams kp = {};
     kp.func = fn;
@@ -766,7 +838,7 @@ KRON_API kron_status kron_varlen_execute_noalloc(kron_varlen_plan* plan, const v
         return KRON_ERR_CUDA;
     int grid = std::max(1, per_sm) * dev.sms;
     grid = (int)std::min<size_t>((size_t)grid, plan->tiles.size());
-    int xbe = plan->xbuf_elems;
+    int xbe = plan->xbuf_bytes;
     void* kargs[2] = {plan->args, &xbe};
     if (cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(kVlThreads), kargs, plan->smem, st) != cudaSuccess)
         return KRON_ERR_CUDA;

@@ -164,3 +164,49 @@ def test_varlen_full_size_sampled(io):
     ref, norm = reference(v, X64, idx)
     assert max_err(v, Y.double().cpu().numpy(), ref, norm, io) <= TOL[io]
     plan.close()
+
+
+@pytest.mark.parametrize("io", ["f32", "bf16"])
+def test_varlen_unaligned_bases_and_permuted_output(io):
+    """Instances start at arbitrary element offsets: X and Y begin one element past
+    a 16-byte boundary, and Y holds the instances in another order with gaps of
+    0..5 elements, so an instance's alignment phase in Y differs from its phase
+    in X.  Every instance matches the oracle and no gap element is written."""
+    import torch
+    v = inputs.make_varlen(3000, seed=15, nmin=1, nmax=16)
+    rng = np.random.default_rng(16)
+    sizes = np.array([v.classes[c][1] ** v.classes[c][0] for c in v.class_of], np.int64)
+    y_off = np.zeros(len(sizes), np.int64)
+    pos = 0
+    for p in rng.permutation(len(sizes)):
+        pos += int(rng.integers(0, 6))
+        y_off[p] = pos
+        pos += int(sizes[p])
+    ytotal = pos + 5
+    if io == "f32":
+        xs, X64 = torch.from_numpy(v.X), v.X.astype(np.float64)
+    else:
+        xs = inputs.to_storage(v.X, io)
+        X64 = inputs.storage_to_f64(xs)
+    xb = torch.zeros(v.total + 1, dtype=torch_dtype(io), device="cuda")
+    xb[1:] = xs.cuda()
+    yb = torch.full((ytotal + 1,), float("nan"), dtype=torch_dtype(io), device="cuda")
+    X, Y = xb[1:], yb[1:]
+    plan = kg.VarlenPlan(classes_of(v), v.class_of, v.x_off, y_off, io=io)
+    ws = plan.alloc_workspace()
+    plan.execute(X, Y, ws)
+    torch.cuda.synchronize()
+    assert kg.device_status() == 0
+    Yh = Y.double().cpu().numpy()
+    covered = np.zeros(ytotal, bool)
+    for p in range(len(sizes)):
+        covered[y_off[p]:y_off[p] + sizes[p]] = True
+    assert np.isnan(Yh[~covered]).all(), "gap written"
+    assert np.isnan(yb[:1].double().cpu().numpy()).all()
+    ref, norm = reference(v, X64)
+    e = 0.0
+    for p, r in ref.items():
+        d = np.maximum(np.abs(Yh[y_off[p]:y_off[p] + sizes[p]] - r) - ABS_FLOOR.get(io, 0.0), 0.0)
+        e = max(e, d.max() / max(norm[p], 1e-300))
+    assert e <= TOL[io], e
+    plan.close()
