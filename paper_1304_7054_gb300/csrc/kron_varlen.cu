@@ -41,7 +41,8 @@
 namespace kron {
 
 constexpr int kVlThreads = 256;
-constexpr int kVlMaxTile = 4096;                       // operand elements per tile
+constexpr int kVlBufBytes = 18432;                     // default budget of one buffer (3-D n = 16 fills it)
+constexpr int kVlMaxBufBytes = 49152;                  // largest buffer a tuned tile may take
 constexpr int kVlKeys = 32;                            // class key = 16 (kind - 2) + n - 1
 
 __host__ __device__ constexpr int sq_sum(int n) { return (n - 1) * n * (2 * n - 1) / 6; }   // sum k^2, k < n
@@ -88,6 +89,22 @@ __device__ __forceinline__ int vl_nx(int key) {
 // Slot of one instance in an operand buffer: its elements plus up to 15 bytes
 // of alignment phase, rounded to 16 bytes.
 __host__ __device__ constexpr int vl_slot_bytes(int nx, int es) { return (nx * es + 15 + 15) / 16 * 16; }
+__host__ __device__ constexpr int vl_max(int a, int b) { return a > b ? a : b; }
+// Exchange elements of one instance (FP32): KP x N (2-D) or KP x N x N (3-D).
+__host__ __device__ constexpr int vl_exq(int kind, int n) { return vl_kp(n) * (kind == 2 ? n : n * n); }
+// Per-instance stride of the operand buffers (bytes).  In 3-D the second
+// contraction writes its FP32 exchange layout over the dead operands, so the
+// slot holds either.
+__host__ __device__ constexpr int vl_xs_bytes(int kind, int n, int es) {
+    return kind == 2 ? vl_slot_bytes(n * n, es)
+                     : (vl_max(vl_slot_bytes(n * n * n, es), 4 * vl_exq(3, n)) + 15) / 16 * 16;
+}
+// Per-instance stride of the exchange buffer (floats).  In 3-D the last
+// contraction writes the results there (contiguous, at their phase in Y), so a
+// slot is 16-byte aligned and holds either.
+__host__ __device__ constexpr int vl_e1_floats(int kind, int n, int es) {
+    return kind == 2 ? vl_exq(2, n) : (vl_max(vl_exq(3, n), vl_slot_bytes(n * n * n, es) / 4) + 3) / 4 * 4;
+}
 
 // Alignment phase (in elements) of element offset `off` of an array at `base`.
 template <typename S>
@@ -103,7 +120,7 @@ __device__ __forceinline__ void vl_issue_loads(const VarlenArgs& a, int4 td, con
                                                uint64_t* bar, uint64_t pol) {
     const int lane = threadIdx.x & 31;
     const int nx = vl_nx(td.x);
-    const int slot = vl_slot_bytes(nx, (int)sizeof(S));
+    const int slot = vl_xs_bytes(td.x < 16 ? 2 : 3, (td.x & 15) + 1, (int)sizeof(S));
     unsigned bytes = 0;
     for (int q = lane; q < td.z; q += 32) {
         const unsigned ph = (((unsigned)(uintptr_t)a.X) + (unsigned)xo[q] * (unsigned)sizeof(S)) & 15u;
@@ -124,13 +141,13 @@ __device__ __forceinline__ void vl_issue_loads(const VarlenArgs& a, int4 td, con
 
 // Issued by warp 0 after the last contraction: per instance, the aligned middle
 // of its run in Y by one bulk copy, the partial granules at both ends by plain
-// stores.  The slot holds the instance at its phase in Y, so slot and Y agree
-// modulo 16 bytes.
+// stores.  Instance q's results start at xt + q * slot plus their phase in Y, so
+// slot and Y agree modulo 16 bytes.
 template <typename S>
-__device__ __forceinline__ void vl_issue_stores(const VarlenArgs& a, int4 td, const int* yo, const unsigned char* xt) {
+__device__ __forceinline__ void vl_issue_stores(const VarlenArgs& a, int4 td, const int* yo, const unsigned char* xt,
+                                                int slot) {
     const int lane = threadIdx.x & 31;
     const int nx = vl_nx(td.x);
-    const int slot = vl_slot_bytes(nx, (int)sizeof(S));
     for (int q = lane; q < td.z; q += 32) {
         S* dst = static_cast<S*>(a.Y) + yo[q];
         const unsigned ph = (unsigned)((uintptr_t)dst & 15u);
@@ -198,22 +215,21 @@ __device__ __forceinline__ void vl_stage_out(S* dst, const f2 (&y)[vl_rows(N) / 
     if constexpr (N & 1) dst[N - 1] = store_cvt<S, float>(f2_lo(y[N / 2]));
 }
 
-// One tile of class (D, N) in buffer xt: instance q's operands at slot q, phase
-// vl_phase(X, xo[q]); its outputs go to the same slot at phase vl_phase(Y, yo[q]),
-// contiguous and column-major.  Exchange layouts put each stage's output pairs
-// next to each other:
-//   2-D   W(l, j)    at j + KP l                 (stage 1 writes pairs along j)
-//   3-D   T(i, j, k) at k + KP i + KP N j        (stage A: pairs along k)
-//         U(i, j, k) at j + KP k + KP N i        (stage B: pairs along j)
+// One tile of class (D, N) in operand buffer xt: instance q's operands at slot q,
+// phase vl_phase(X, xo[q]).  Its results, contiguous and column-major at phase
+// vl_phase(Y, yo[q]), go to operand slot q (2-D) or exchange slot q (3-D).
+// Exchange layouts put each stage's output pairs next to each other:
+//   2-D   W(l, j)    at j + KP l            in ex1  (stage 1 writes pairs along j)
+//   3-D   T(i, j, k) at k + KP i + KP N j   in ex1  (stage A: pairs along k)
+//         U(i, j, k) at j + KP k + KP N i   in xt   (stage B: pairs along j)
 // and the last stage writes pairs along i.
 template <typename S, int N, int D>
-__device__ __forceinline__ void vl_tile(const VarlenArgs& a, int4 td, unsigned char* xt, float* ex1, float* ex2,
-                                        const int* xo, const int* yo) {
-    constexpr int NX = ipow(N, D);
+__device__ __forceinline__ void vl_tile(const VarlenArgs& a, int4 td, unsigned char* xt, float* ex1, const int* xo,
+                                        const int* yo) {
     constexpr int KP = vl_kp(N);
     constexpr int R = vl_rows(N) / 2;
-    constexpr int EXQ = KP * ipow(N, D - 1);   // exchange elements per instance
-    constexpr int SLOT = vl_slot_bytes(NX, (int)sizeof(S));
+    constexpr int EXQ = vl_e1_floats(D, N, (int)sizeof(S));   // exchange stride per instance (floats)
+    constexpr int SLOT = vl_xs_bytes(D, N, (int)sizeof(S));   // operand stride per instance (bytes)
     const float* m1 = a.coef + vl_slot(D, N);
     const float* m2 = m1 + vl_rows(N) * N;
     const float* m3 = m2 + vl_rows(N) * N;
@@ -267,43 +283,43 @@ __device__ __forceinline__ void vl_tile(const VarlenArgs& a, int4 td, unsigned c
             for (int m = 0; m < N; ++m) t[m] = tr[KP * N * m];
             f2 u[R];
             vl_contract<N>(m2, t, u);
-            vl_store_pairs<N>(ex2 + q * EXQ + KP * k + KP * N * i, u);
+            vl_store_pairs<N>(reinterpret_cast<float*>(xt + q * SLOT) + KP * k + KP * N * i, u);
         }
         __syncthreads();
         for (int f = tid; f < F; f += kVlThreads) {   // stage C: mode 1, fibers (j, k)
             const int q = f / (N * N), r = f - q * (N * N);
             const int j = r % N, k = r / N;
-            const float* ur = ex2 + q * EXQ + j + KP * k;
+            const float* ur = reinterpret_cast<const float*>(xt + q * SLOT) + j + KP * k;
             float u[N];
 #pragma unroll
             for (int l = 0; l < N; ++l) u[l] = ur[KP * N * l];
             f2 y[R];
             vl_contract<N>(m1, u, y);
-            vl_stage_out<S, N>(reinterpret_cast<S*>(xt + q * SLOT) + vl_phase<S>(Y, yo[q]) + N * (j + N * k), y);
+            vl_stage_out<S, N>(reinterpret_cast<S*>(ex1 + q * EXQ) + vl_phase<S>(Y, yo[q]) + N * (j + N * k), y);
         }
     }
 }
 
 template <typename S, int D>
-__device__ __forceinline__ void vl_dispatch_n(const VarlenArgs& a, int4 td, unsigned char* xt, float* ex1, float* ex2,
+__device__ __forceinline__ void vl_dispatch_n(const VarlenArgs& a, int4 td, unsigned char* xt, float* ex1,
                                               const int* xo, const int* yo) {
     switch ((td.x & 15) + 1) {
-        case 1: vl_tile<S, 1, D>(a, td, xt, ex1, ex2, xo, yo); break;
-        case 2: vl_tile<S, 2, D>(a, td, xt, ex1, ex2, xo, yo); break;
-        case 3: vl_tile<S, 3, D>(a, td, xt, ex1, ex2, xo, yo); break;
-        case 4: vl_tile<S, 4, D>(a, td, xt, ex1, ex2, xo, yo); break;
-        case 5: vl_tile<S, 5, D>(a, td, xt, ex1, ex2, xo, yo); break;
-        case 6: vl_tile<S, 6, D>(a, td, xt, ex1, ex2, xo, yo); break;
-        case 7: vl_tile<S, 7, D>(a, td, xt, ex1, ex2, xo, yo); break;
-        case 8: vl_tile<S, 8, D>(a, td, xt, ex1, ex2, xo, yo); break;
-        case 9: vl_tile<S, 9, D>(a, td, xt, ex1, ex2, xo, yo); break;
-        case 10: vl_tile<S, 10, D>(a, td, xt, ex1, ex2, xo, yo); break;
-        case 11: vl_tile<S, 11, D>(a, td, xt, ex1, ex2, xo, yo); break;
-        case 12: vl_tile<S, 12, D>(a, td, xt, ex1, ex2, xo, yo); break;
-        case 13: vl_tile<S, 13, D>(a, td, xt, ex1, ex2, xo, yo); break;
-        case 14: vl_tile<S, 14, D>(a, td, xt, ex1, ex2, xo, yo); break;
-        case 15: vl_tile<S, 15, D>(a, td, xt, ex1, ex2, xo, yo); break;
-        case 16: vl_tile<S, 16, D>(a, td, xt, ex1, ex2, xo, yo); break;
+        case 1: vl_tile<S, 1, D>(a, td, xt, ex1, xo, yo); break;
+        case 2: vl_tile<S, 2, D>(a, td, xt, ex1, xo, yo); break;
+        case 3: vl_tile<S, 3, D>(a, td, xt, ex1, xo, yo); break;
+        case 4: vl_tile<S, 4, D>(a, td, xt, ex1, xo, yo); break;
+        case 5: vl_tile<S, 5, D>(a, td, xt, ex1, xo, yo); break;
+        case 6: vl_tile<S, 6, D>(a, td, xt, ex1, xo, yo); break;
+        case 7: vl_tile<S, 7, D>(a, td, xt, ex1, xo, yo); break;
+        case 8: vl_tile<S, 8, D>(a, td, xt, ex1, xo, yo); break;
+        case 9: vl_tile<S, 9, D>(a, td, xt, ex1, xo, yo); break;
+        case 10: vl_tile<S, 10, D>(a, td, xt, ex1, xo, yo); break;
+        case 11: vl_tile<S, 11, D>(a, td, xt, ex1, xo, yo); break;
+        case 12: vl_tile<S, 12, D>(a, td, xt, ex1, xo, yo); break;
+        case 13: vl_tile<S, 13, D>(a, td, xt, ex1, xo, yo); break;
+        case 14: vl_tile<S, 14, D>(a, td, xt, ex1, xo, yo); break;
+        case 15: vl_tile<S, 15, D>(a, td, xt, ex1, xo, yo); break;
+        case 16: vl_tile<S, 16, D>(a, td, xt, ex1, xo, yo); break;
     }
 }
 
@@ -353,15 +369,14 @@ __global__ void __launch_bounds__(kVlThreads) varlen_kernel(const __grid_constan
         }
         const int4 d3 = tile + 3 * G < a.ntiles ? a.tiles[tile + 3 * G] : none;
         if (tid < 32) {
-            // Operands of this tile (first iteration only) and of the next one; the
-            // other buffer's last results have left shared memory before it is reused.
+            // The previous tile's results have left shared memory (the other operand
+            // buffer or the exchange buffer) before either is written again; then the
+            // operands of this tile (first iteration only) and of the next one.
+            bulk_wait_read();
+            __syncwarp();
             for (int u = it == 0 ? 0 : 1; u < 2; ++u) {
                 const int4 du = u ? d1 : d0;
                 if (!du.z) break;
-                if (u) {
-                    bulk_wait_read();
-                    __syncwarp();
-                }
                 vl_issue_loads<S>(a, du, ring + 2 * kVlThreads * (u ? s1 : s0), xbuf + (b ^ u) * xbuf_bytes,
                                   &full[b ^ u], pol);
             }
@@ -377,20 +392,23 @@ __global__ void __launch_bounds__(kVlThreads) varlen_kernel(const __grid_constan
             return;
         }
         const int key = d0.x;
-        const int P = a.cls[key].P;
         const int n = (key & 15) + 1;
-        // exchange buffer 2 starts after P * (per-instance size of buffer 1)
-        float* ex2 = ex1 + (size_t)P * vl_kp(n) * (key < 16 ? n : n * n);
         unsigned char* xt = xbuf + b * xbuf_bytes;
         const int* xo = ring + 2 * kVlThreads * s0;
         const int* yo = xo + kVlThreads;
         if (key < 16)
-            vl_dispatch_n<S, 2>(a, d0, xt, ex1, ex2, xo, yo);
+            vl_dispatch_n<S, 2>(a, d0, xt, ex1, xo, yo);
         else
-            vl_dispatch_n<S, 3>(a, d0, xt, ex1, ex2, xo, yo);
+            vl_dispatch_n<S, 3>(a, d0, xt, ex1, xo, yo);
         fence_proxy_async_smem();   // results visible to the bulk copies
         __syncthreads();
-        if (tid < 32) vl_issue_stores<S>(a, d0, yo, xt);
+        if (tid < 32) {
+            if (key < 16)
+                vl_issue_stores<S>(a, d0, yo, xt, vl_xs_bytes(2, n, (int)sizeof(S)));
+            else
+                vl_issue_stores<S>(a, d0, yo, reinterpret_cast<const unsigned char*>(ex1),
+                                   4 * vl_e1_floats(3, n, (int)sizeof(S)));
+        }
         if (tid < d2.z) {
             ring[2 * kVlThreads * s2 + tid] = xo2;
             ring[2 * kVlThreads * s2 + kVlThreads + tid] = yo2;
@@ -406,18 +424,19 @@ __global__ void __launch_bounds__(kVlThreads) varlen_kernel(const __grid_constan
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
-static size_t vl_ex_floats(int kind, int n, int P) {
-    const size_t exq = (size_t)vl_kp(n) * (kind == 2 ? n : n * n);
-    return (size_t)P * exq * (kind == 2 ? 1 : 2);
+// Largest tile of class (kind, n) whose operand and exchange buffers stay within
+// `budget` bytes each.
+static int vl_max_P(int kind, int n, size_t es, int budget) {
+    const int xs = vl_xs_bytes(kind, n, (int)es), ex = 4 * vl_e1_floats(kind, n, (int)es);
+    return std::max(1, std::min(kVlThreads, budget / std::max(xs, ex)));
 }
 
-static int vl_default_P(int kind, int n) {
+// Default tile: as many instances as one fiber per thread covers in every
+// contraction (a second, partly filled round of fibers would leave most threads
+// waiting at the barrier), within the default buffer budget.
+static int vl_default_P(int kind, int n, size_t es) {
     const int fpi = kind == 2 ? n : n * n;
-    const int nx = kind == 2 ? n * n : n * n * n;
-    int P = std::max(1, (kVlThreads + fpi - 1) / fpi);
-    P = std::min(P, kVlMaxTile / nx);
-    P = std::min(P, kVlThreads);
-    return std::max(1, P);
+    return std::max(1, std::min(kVlThreads / fpi, vl_max_P(kind, n, es, kVlBufBytes)));
 }
 
 }  // namespace kron
@@ -476,7 +495,6 @@ static kron_status vl_build(kron_varlen_plan* p) {
     for (int key = 0; key < kVlKeys; ++key) {
         if (by[key].empty()) continue;
         const int kind = key < 16 ? 2 : 3, n = (key & 15) + 1;
-        const int nx = kind == 2 ? n * n : n * n * n;
         const int P = p->P[key];
         const int64_t start = (int64_t)p->order.size();
         for (int64_t i : by[key]) p->order.push_back(i);
@@ -486,8 +504,8 @@ static kron_status vl_build(kron_varlen_plan* p) {
             const int c = (int)std::min<int64_t>(P, cnt - s);
             tl.push_back(T{flops * c, make_int4(key, (int)(start + s), c, 0)});
         }
-        max_x = std::max(max_x, (size_t)P * vl_slot_bytes(nx, (int)es));
-        max_smem_rest = std::max(max_smem_rest, vl_ex_floats(kind, n, P) * sizeof(float));
+        max_x = std::max(max_x, (size_t)P * vl_xs_bytes(kind, n, (int)es));
+        max_smem_rest = std::max(max_smem_rest, (size_t)P * vl_e1_floats(kind, n, (int)es) * sizeof(float));
     }
     if (p->order.size() > (size_t)INT32_MAX) return KRON_ERR_NOT_SUPPORTED;
     std::stable_sort(tl.begin(), tl.end(), [](const T& a, const T& b) { return a.work > b.work; });
@@ -636,7 +654,7 @@ KRON_API kron_status kron_varlen_plan_create(kron_varlen_plan** plan, int num_cl
         }
         p->present[key] = 1;
         key_of_class[c] = key;
-        const int n = d.n, nn = n * n;
+        const int n = d.n;
         const int rows = vl_rows(n);
         float* slot = p->args->coef + vl_slot(d.kind, n);
         // mode 1 first: 2-D (Y = B X A^T) B, A; 3-D C, B, A
@@ -649,8 +667,8 @@ KRON_API kron_status kron_varlen_plan_create(kron_varlen_plan** plan, int num_cl
         }
         int tp = 0, td = 0;
         kron_get_tile_config(d.kind, n, io, (kron_compute)kVarlenTag, &tp, &td);
-        const int nx = d.kind == 2 ? nn : nn * n;
-        p->P[key] = (tp > 0 && tp * nx <= kVlMaxTile && tp <= kVlThreads) ? tp : vl_default_P(d.kind, n);
+        p->P[key] = (tp > 0 && tp <= vl_max_P(d.kind, n, elem_size(io), kVlMaxBufBytes)) ? tp
+                                                                                     : vl_default_P(d.kind, n, elem_size(io));
     }
     p->cls_of.resize(batch_count);
     p->xoff.assign(h_x_off, h_x_off + batch_count);
@@ -762,8 +780,7 @@ KRON_API kron_status kron_varlen_tune(kron_varlen_plan* plan, const void* X, voi
     for (size_t w = 0; w < work.size() && st == KRON_OK; ++w) {
         const int key = work[w].second;
         const int kind = key < 16 ? 2 : 3, n = (key & 15) + 1;
-        const int nx = kind == 2 ? n * n : n * n * n;
-        const int pmax = std::max(1, std::min(kVlThreads, kVlMaxTile / nx));
+        const int pmax = vl_max_P(kind, n, elem_size(plan->io), kVlMaxBufBytes);
         const int cur = plan->P[key];
         int best_P = cur;
         for (int cand : {cur / 2, cur * 2, cur * 4, cur / 4, cur + cur / 2}) {
