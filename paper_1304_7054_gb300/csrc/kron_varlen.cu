@@ -41,7 +41,7 @@
 namespace kron {
 
 constexpr int kVlThreads = 256;
-constexpr int kVlBufBytes = 18432;                     // default budget of one buffer (3-D n = 16 fills it)
+constexpr int kVlBufBytes = 22528;                     // default budget of one buffer
 constexpr int kVlMaxBufBytes = 49152;                  // largest buffer a tuned tile may take
 constexpr int kVlKeys = 32;                            // class key = 16 (kind - 2) + n - 1
 
@@ -431,12 +431,13 @@ static int vl_max_P(int kind, int n, size_t es, int budget) {
     return std::max(1, std::min(kVlThreads, budget / std::max(xs, ex)));
 }
 
-// Default tile: as many instances as one fiber per thread covers in every
-// contraction (a second, partly filled round of fibers would leave most threads
-// waiting at the barrier), within the default buffer budget.
+// Default tile, within the default buffer budget: as many instances as one
+// round of fibers (one per thread) covers in 2-D, two rounds in 3-D (the
+// tuner's choice on the mixed batch for most 3-D sizes: a second round halves
+// the share of the barrier waits).
 static int vl_default_P(int kind, int n, size_t es) {
-    const int fpi = kind == 2 ? n : n * n;
-    return std::max(1, std::min(kVlThreads / fpi, vl_max_P(kind, n, es, kVlBufBytes)));
+    const int fibers = kind == 2 ? kVlThreads / n : 2 * kVlThreads / (n * n);
+    return std::max(1, std::min(fibers, vl_max_P(kind, n, es, kVlBufBytes)));
 }
 
 }  // namespace kron
