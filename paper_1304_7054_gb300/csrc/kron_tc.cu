@@ -301,6 +301,10 @@ struct TcArgs3 {
     unsigned* err;
 };
 
+// n < 16: T has its own 16 KB buffer, so the operand buffer is free after modes
+// 1 and 2 and the next instance is fetched while mode 3 runs.  n = 16: T rows
+// overwrite the operand planes (a separate T buffer halves the resident warps and
+// measured 1.32x slower), so the next fetch waits for mode 3.
 template <int N>
 struct Tc3Layout {
     static constexpr uint32_t XB = (uint32_t)round_up((size_t)N * N * N * 4, 128);  // FP32 instance
@@ -481,6 +485,17 @@ __global__ void __launch_bounds__(32 * kTc3Warps) tc3_kernel(const __grid_consta
             if (two) tc3_plane_store(tb, p + 1, g, t, z1);
         }
         __syncwarp();
+        auto fetch_next = [&]() {
+            if (lane == 0) {
+                const int64_t next = inst + nwarps;
+                if (next < a.batch) {
+                    fence_proxy_async_smem();
+                    mbar_arrive_expect_tx(bar, NX * 4);
+                    bulk_g2s(xs, static_cast<const float*>(a.X) + next * NX, NX * 4, bar, pol);
+                }
+            }
+        };
+        if constexpr (!L::INPLACE) fetch_next();   // the operand planes are no longer read
 
         // ---- mode 3, two row blocks per step ---------------------------------------------
         float* yq = static_cast<float*>(a.Y) + inst * NX;
@@ -489,15 +504,8 @@ __global__ void __launch_bounds__(32 * kTc3Warps) tc3_kernel(const __grid_consta
             tc3_rows<N>(a, yq, tb_s, mt, lane, m3h, m3l);
             if (mt + 1 < N) tc3_rows<N>(a, yq, tb_s, mt + 1, lane, m3h, m3l);
         }
-        __syncwarp();   // T and the operand planes are free: fetch the next instance
-        if (lane == 0) {
-            const int64_t next = inst + nwarps;
-            if (next < a.batch) {
-                fence_proxy_async_smem();
-                mbar_arrive_expect_tx(bar, NX * 4);
-                bulk_g2s(xs, static_cast<const float*>(a.X) + next * NX, NX * 4, bar, pol);
-            }
-        }
+        __syncwarp();   // T is free (in place: so are the operand planes)
+        if constexpr (L::INPLACE) fetch_next();
     }
 }
 

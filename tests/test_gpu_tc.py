@@ -117,6 +117,16 @@ def test_bf16x3_3d_even_sizes(n):
     assert err <= 1e-5, err
 
 
+@pytest.mark.parametrize("n", [10, 16])
+@pytest.mark.parametrize("batch", [1, 3, 4099])
+def test_bf16x3_3d_ragged_and_wrapping_batches(n, batch):
+    """Batches that leave warps idle and batches that wrap every warp several
+    times (n = 10 fetches the next instance while mode 3 runs, n = 16 after it)."""
+    b = inputs.make_batch(3, n, batch, seed=420 + batch + n, x_dist="normal")
+    Y, X64 = run_gpu(b, io="f32", compute="bf16x3", guard=16)
+    assert max_norm_err(Y, oracle_ref(b, X64), b, X64) <= 1e-5
+
+
 def test_bf16x3_3d_alpha_beta():
     n = 16
     b = inputs.make_batch(3, n, 37, seed=410, x_dist="normal")
