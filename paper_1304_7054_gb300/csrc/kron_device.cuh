@@ -117,6 +117,12 @@ __device__ __forceinline__ void bulk_s2g(void* dst, const void* src, unsigned by
                  "r"(bytes)
                  : "memory");
 }
+// As bulk_s2g, with an L2 cache policy for the written lines.
+__device__ __forceinline__ void bulk_s2g_hint(void* dst, const void* src, unsigned bytes, uint64_t policy) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group.L2::cache_hint [%0], [%1], %2, %3;" ::"l"(dst),
+                 "r"(smem_u32(src)), "r"(bytes), "l"(policy)
+                 : "memory");
+}
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 // The shared-memory sources of this thread's bulk stores have been read.
 __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }

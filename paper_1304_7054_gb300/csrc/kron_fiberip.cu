@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(kFiThreads, 4) fiberip_kernel(const __grid_con
             // whole 16-byte chunks by bulk copy; a ragged last tile's tail is
             // stored by the compute threads
             const unsigned bytes = ((unsigned)c * NX * 4u) & ~15u;
-            if (lane == 0 && bytes) bulk_s2g(Y + i0 * NX, ring + s * tile_words, bytes);
+            if (lane == 0 && bytes) bulk_s2g_hint(Y + i0 * NX, ring + s * tile_words, bytes, pol);
             bulk_commit();
         };
         int it = 0;

@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(kK1Threads) kron1_kernel(const __grid_constant
             fence_proxy_async_smem();
             __syncwarp();
             if (lane == 0) {
-                bulk_s2g(Y + p0 * a.ma, sb, bytes);
+                bulk_s2g_hint(Y + p0 * a.ma, sb, bytes, l2_evict_first_policy());
                 bulk_commit();
             }
         } else if (live) {

@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(kThreads, 6) pair16_kernel(const __grid_consta
             const int64_t i0 = t * kTileP;
             const int c = (int)min((int64_t)kTileP, a.batch - i0);
             if (lane < c) {
-                bulk_s2g(Y + (i0 + lane) * kNX, ring + s * kTileWords + slot_of(lane), kNX * 4u);
+                bulk_s2g_hint(Y + (i0 + lane) * kNX, ring + s * kTileWords + slot_of(lane), kNX * 4u, pol);
                 bulk_commit();
             }
         };
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(kThreads, 6) pair16h_kernel(const __grid_const
         auto store_tile = [&](int s, int64_t t) {
             const int64_t i0 = t * kTileP;
             const int c = (int)min((int64_t)kTileP, a.batch - i0);
-            if (lane < c) bulk_s2g(Y + (i0 + lane) * kNX, slot(s, lane), kNX * 2u);
+            if (lane < c) bulk_s2g_hint(Y + (i0 + lane) * kNX, slot(s, lane), kNX * 2u, pol);
             bulk_commit();
         };
         int it = 0;

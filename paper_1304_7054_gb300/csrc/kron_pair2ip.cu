@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(kIpThreads, 6) pair2ip_kernel(const __grid_con
         auto store_tile = [&](int s, int64_t t) {
             const int64_t i0 = t * P;
             const int c = (int)min((int64_t)P, a.batch - i0);
-            if (lane == 0) bulk_s2g(Y + i0 * L::NX, ring + s * tile_words, (unsigned)c * L::NX * 4u);
+            if (lane == 0) bulk_s2g_hint(Y + i0 * L::NX, ring + s * tile_words, (unsigned)c * L::NX * 4u, pol);
             bulk_commit();
         };
         int it = 0;

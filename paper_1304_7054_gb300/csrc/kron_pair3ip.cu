@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(kThreads, 5) pair3ip_kernel(const __grid_const
         float* Y = static_cast<float*>(a.Y);
         const float* X = static_cast<const float*>(a.X);
         auto store_inst = [&](int s, int64_t p) {
-            if (lane < 16) bulk_s2g(Y + p * kNX + 256 * lane, ring + s * kInstWords + kPlane * lane, 1024u);
+            if (lane < 16) bulk_s2g_hint(Y + p * kNX + 256 * lane, ring + s * kInstWords + kPlane * lane, 1024u, pol);
             bulk_commit();
         };
         int it = 0;
@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(kThreads, 4) pair3pk_kernel(const __grid_const
         auto store_tile = [&](int s, int64_t t) {
             const int64_t i0 = t * kPkP;
             const int c = (int)min((int64_t)kPkP, a.batch - i0);
-            if (lane == 0) bulk_s2g(Y + i0 * NX, ring + s * kPkP * NX, (unsigned)c * NX * 4u);
+            if (lane == 0) bulk_s2g_hint(Y + i0 * NX, ring + s * kPkP * NX, (unsigned)c * NX * 4u, pol);
             bulk_commit();
         };
         int it = 0;

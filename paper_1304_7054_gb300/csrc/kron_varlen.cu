@@ -148,6 +148,7 @@ __device__ __forceinline__ void vl_issue_stores(const VarlenArgs& a, int4 td, co
                                                 int slot) {
     const int lane = threadIdx.x & 31;
     const int nx = vl_nx(td.x);
+    const uint64_t pol = l2_evict_first_policy();
     for (int q = lane; q < td.z; q += 32) {
         S* dst = static_cast<S*>(a.Y) + yo[q];
         const unsigned ph = (unsigned)((uintptr_t)dst & 15u);
@@ -160,8 +161,9 @@ __device__ __forceinline__ void vl_issue_stores(const VarlenArgs& a, int4 td, co
         }
         const unsigned mid = (total - head) & ~15u;
         for (unsigned e = 0; e < head / sizeof(S); ++e) dst[e] = src[e];
-        if (mid) bulk_s2g(reinterpret_cast<unsigned char*>(dst) + head,
-                          reinterpret_cast<const unsigned char*>(src) + head, mid);
+        if (mid)
+            bulk_s2g_hint(reinterpret_cast<unsigned char*>(dst) + head, reinterpret_cast<const unsigned char*>(src) + head,
+                          mid, pol);
         for (unsigned e = (head + mid) / sizeof(S); e < (unsigned)nx; ++e) dst[e] = src[e];
     }
     bulk_commit();
