@@ -238,7 +238,13 @@ KRON_API kron_status kron_autotune(kron_stream_t stream, int kind, int n, int64_
  * h_y_off[p] of Y; instances are contiguous (minimal leading dimensions),
  * alpha = 1, beta = 0.  Storage: KRON_R32F or KRON_R16BF / KRON_R16F
  * (components float).  X and Y may span at most 2^31 - 1 elements each
- * (KRON_ERR_NOT_SUPPORTED beyond).
+ * (KRON_ERR_NOT_SUPPORTED beyond).  X and Y need only element alignment, and
+ * the offsets are arbitrary: the kernel copies the 16-byte-aligned span around
+ * each operand and writes each result's aligned middle by bulk copy, its ends
+ * by plain stores, so nothing outside [h_y_off[p], h_y_off[p] + n^kind) is
+ * written.  Results of different instances must not overlap
+ * (KRON_ERR_INVALID_VALUE at plan creation); X and Y must not overlap
+ * (KRON_ERR_ALIAS at execute).
  *
  * kron_varlen_plan_create copies the host metadata, sorts instances by class,
  * chooses per-class tile sizes (from the tuning cache when present) and
