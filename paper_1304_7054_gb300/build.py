@@ -93,14 +93,40 @@ FAMILY_SOURCES = {
 }
 
 
+def strip_comments(src: str) -> str:
+    """C/C++ source without its comments (string and character literals kept),
+    so that a comment edit leaves the code's hash unchanged."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        else:
+            out.append(c)
+            i += 1
+    return "".join(out)
+
+
 def source_hash(family: str | None = None) -> str:
-    """Hash of the sources of one kernel family (all sources if None); a stored
-    profile applies only while this hash is unchanged."""
+    """Hash of the code (comments removed, whitespace runs collapsed) of one kernel
+    family's sources, or of all sources if None; a stored profile applies only
+    while it is unchanged."""
     import hashlib
     h = hashlib.sha256()
     files = ([os.path.join(CSRC, f) for f in FAMILY_SOURCES[family]] if family
              else sorted(glob.glob(os.path.join(CSRC, "*"))))
     for f in files:
         h.update(os.path.basename(f).encode())
-        h.update(open(f, "rb").read())
+        h.update(" ".join(strip_comments(open(f, encoding="utf-8").read()).split()).encode())
     return h.hexdigest()[:16]

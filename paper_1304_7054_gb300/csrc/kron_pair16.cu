@@ -1,4 +1,6 @@
-// 2-D FP32 pair kernel for n = 16 with the mode exchange done in place.
+// 2-D pair kernels for n = 16 with the mode exchange done in place: FP32
+// storage (pair16_kernel), and bf16 / f16 storage with FP32 arithmetic
+// (pair16h_kernel, further below).
 //
 // The two contractions are those of the generic pair kernel (Sec. 2.1, the
 // 2-D case of Algorithm 1: mode 2 with M2 = op(A) as pairs of fibers, then
@@ -19,8 +21,9 @@
 //    copy (TMA) per instance, so L2 receives whole lines.
 //  * One producer warp streams tiles in and results out through a ring of
 //    buffers (full / empty mbarriers), one 1 KB bulk copy per instance each
-//    way; the four compute warps never issue a global memory access (except
-//    the reads of Y that beta != 0 needs).
+//    way, both with an L2 evict-first policy (the data is streamed once); the
+//    four compute warps never issue a global memory access (except the reads
+//    of Y that beta != 0 needs).
 #include "kron_pair.cuh"
 
 namespace kron {
