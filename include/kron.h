@@ -93,6 +93,16 @@ KRON_API const char* kron_status_string(kron_status s);
 KRON_API int kron_version(void);
 
 /*
+ * kron_check_device_buffer -- the check every call makes on its X, Y (and
+ * workspace) before launching: KRON_OK when [p, p + bytes) lies inside one
+ * device or managed allocation of the current context.  KRON_ERR_INVALID_VALUE
+ * for a null, host or unregistered pointer, or an extent past the end of the
+ * allocation (such a launch would fault); KRON_ERR_CUDA when no device is
+ * usable.  Launches nothing.
+ */
+KRON_API kron_status kron_check_device_buffer(const void* p, size_t bytes);
+
+/*
  * kron2_batched -- the paper's TKRON2 (Sec. 3) with the component order above.
  *
  *   op(A): ma x na, stored as A (lda >= rows of the stored matrix: ma if

@@ -32,6 +32,7 @@ _I, _L, _P, _C, _S = ctypes.c_int, ctypes.c_int64, ctypes.c_void_p, ctypes.c_cha
 SIGNATURES = {
     "kron_status_string": ([_I], ctypes.c_char_p),
     "kron_version": ([], _I),
+    "kron_check_device_buffer": ([_P, _S], _I),
     "kron2_batched": ([_P, _C, _C, _C, _I, _I, _I, _I, _L, _P, _P, _I, _P, _I, _P, _I, _L, _P, _P, _I, _L,
                        _I, _I], _I),
     "kron3_batched": ([_P, _C, _C, _C, _I, _I, _I, _I, _I, _I, _L, _P, _P, _I, _P, _I, _P, _I, _P, _I, _I,
@@ -116,6 +117,17 @@ def _comp_buffer(M, ctype):
     return np.ascontiguousarray(M.ravel()), None
 
 
+def _device_operand(t, need, name):
+    """Device address of tensor t, after checking that it lives on a GPU and, when
+    contiguous, holds the `need` elements the call touches (the library checks
+    the same range against the allocation before it launches anything)."""
+    if not getattr(t, "is_cuda", False):
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if need > 0 and t.is_contiguous() and t.numel() < need:
+        raise ValueError(f"{name} holds {t.numel()} elements but the call reaches element {need - 1}")
+    return t.data_ptr()
+
+
 def _scalar(v, ctype):
     return (ctypes.c_double if ctype == np.float64 else ctypes.c_float)(v)
 
@@ -140,9 +152,12 @@ def kron2_batched(A, B, X, Y, *, ma, na, mb, nb, batch, alpha=1.0, beta=0.0, tra
     ldy = ldy or mb
     ldyp = ldy * ma if ldyp is None else ldyp
     al, be = _scalar(alpha, ctype), _scalar(beta, ctype)
+    xr, xc = (nb, na) if tx == "N" else (na, nb)
+    xp = _device_operand(X, (batch - 1) * ldxp + ldx * (xc - 1) + xr if batch > 0 else 0, "X")
+    yp = _device_operand(Y, (batch - 1) * ldyp + ldy * (ma - 1) + mb if batch > 0 else 0, "Y")
     st = L.kron2_batched(_stream_handle(stream), ta.encode(), tb.encode(), tx.encode(), ma, na, mb, nb, batch,
-                         ctypes.addressof(al), Ab.ctypes.data, lda, Bb.ctypes.data, ldb, X.data_ptr(), ldx, ldxp,
-                         ctypes.addressof(be), Y.data_ptr(), ldy, ldyp, io, COMPUTE[compute])
+                         ctypes.addressof(al), Ab.ctypes.data, lda, Bb.ctypes.data, ldb, xp, ldx, ldxp,
+                         ctypes.addressof(be), yp, ldy, ldyp, io, COMPUTE[compute])
     _check(st, "kron2_batched")
     return Y
 
@@ -170,9 +185,11 @@ def kron3_batched(A, B, C, X, Y, *, ma, na, mb, nb, mc, nc, batch, alpha=1.0, be
     ldy2 = ldy2 or ldy * mb
     ldyp = ldy2 * ma if ldyp is None else ldyp
     al, be = _scalar(alpha, ctype), _scalar(beta, ctype)
+    xp = _device_operand(X, (batch - 1) * ldxp + ldx2 * (na - 1) + ldx * (nb - 1) + nc if batch > 0 else 0, "X")
+    yp = _device_operand(Y, (batch - 1) * ldyp + ldy2 * (ma - 1) + ldy * (mb - 1) + mc if batch > 0 else 0, "Y")
     st = L.kron3_batched(_stream_handle(stream), ta.encode(), tb.encode(), tc.encode(), ma, na, mb, nb, mc, nc,
                          batch, ctypes.addressof(al), Ab.ctypes.data, lda, Bb.ctypes.data, ldb, Cb.ctypes.data,
-                         ldc, X.data_ptr(), ldx, ldx2, ldxp, ctypes.addressof(be), Y.data_ptr(), ldy, ldy2, ldyp,
+                         ldc, xp, ldx, ldx2, ldxp, ctypes.addressof(be), yp, ldy, ldy2, ldyp,
                          io, COMPUTE[compute])
     _check(st, "kron3_batched")
     return Y
@@ -192,8 +209,10 @@ def kron1_batched(A, X, Y, *, ma, na, batch, alpha=1.0, beta=0.0, transa="N", ld
     ldxp = na if ldxp is None else ldxp
     ldyp = ma if ldyp is None else ldyp
     al, be = _scalar(alpha, ctype), _scalar(beta, ctype)
+    xp = _device_operand(X, (batch - 1) * ldxp + na if batch > 0 else 0, "X")
+    yp = _device_operand(Y, (batch - 1) * ldyp + ma if batch > 0 else 0, "Y")
     st = L.kron1_batched(_stream_handle(stream), ta.encode(), ma, na, batch, ctypes.addressof(al), Ab.ctypes.data,
-                         lda, X.data_ptr(), ldxp, ctypes.addressof(be), Y.data_ptr(), ldyp, io, COMPUTE[compute])
+                         lda, xp, ldxp, ctypes.addressof(be), yp, ldyp, io, COMPUTE[compute])
     _check(st, "kron1_batched")
     return Y
 
@@ -214,11 +233,23 @@ def gemm_a_batched(A, B, C, *, m, n, k, batch, alpha=1.0, beta=0.0, transa="N", 
     ldc = ldc or m
     ldc2 = ldc * n if ldc2 is None else ldc2
     al, be = _scalar(alpha, ctype), _scalar(beta, ctype)
+    aext = lda * (m - 1) + k if ta == "T" else lda * (k - 1) + m
+    ap = _device_operand(A, (batch - 1) * lda2 + aext if batch > 0 else 0, "A")
+    cp = _device_operand(C, (batch - 1) * ldc2 + ldc * (n - 1) + m if batch > 0 else 0, "C")
     st = L.kron_gemm_a_batched(_stream_handle(stream), ta.encode(), tb.encode(), m, n, k, ctypes.addressof(al),
-                               A.data_ptr(), lda, lda2, Bb.ctypes.data, ldb, ctypes.addressof(be), C.data_ptr(),
+                               ap, lda, lda2, Bb.ctypes.data, ldb, ctypes.addressof(be), cp,
                                ldc, ldc2, batch, grid_size, io, COMPUTE[compute])
     _check(st, "kron_gemm_a_batched")
     return C
+
+
+def check_device_buffer(t, nbytes=None) -> int:
+    """kron_check_device_buffer on tensor t (or a raw address with nbytes): the
+    status the library's own pre-launch check gives for that range."""
+    ptr = t.data_ptr() if hasattr(t, "data_ptr") else int(t)
+    if nbytes is None:
+        nbytes = t.numel() * t.element_size()
+    return load_library().kron_check_device_buffer(ptr, nbytes)
 
 
 def device_status(stream=None) -> int:
@@ -242,7 +273,9 @@ def get_tile_config(kind, n, io, compute="native"):
 def autotune(kind, n, batch, X, Y, compute="native", stream=None):
     """Time the candidate tile configurations on X -> Y and keep the fastest."""
     p, d = ctypes.c_int(), ctypes.c_int()
-    _check(load_library().kron_autotune(_stream_handle(stream), kind, n, batch, X.data_ptr(), Y.data_ptr(),
+    need = batch * n ** kind
+    xp, yp = _device_operand(X, need, "X"), _device_operand(Y, need, "Y")
+    _check(load_library().kron_autotune(_stream_handle(stream), kind, n, batch, xp, yp,
                                         _io_of(X), COMPUTE[compute], ctypes.byref(p), ctypes.byref(d)),
            "kron_autotune")
     return p.value, d.value
@@ -285,6 +318,11 @@ class VarlenPlan:
                                          DTYPES[io], COMPUTE[compute]), "kron_varlen_plan_create")
         self.handle = h
         self.io = io
+        # elements of X and Y the plan reaches (the library has validated the metadata)
+        sizes = np.array([int(c[1]) ** int(c[0]) for c in classes] or [0], dtype=np.int64)
+        nx = sizes[self._cls] if self.batch else np.zeros(0, np.int64)
+        self.x_extent = int((self._xo + nx).max()) if self.batch else 0
+        self.y_extent = int((self._yo + nx).max()) if self.batch else 0
 
     def workspace_size(self) -> int:
         s = ctypes.c_size_t()
@@ -296,22 +334,30 @@ class VarlenPlan:
         torch = _torch()
         return torch.empty(max(1, self.workspace_size()), dtype=torch.uint8, device=device or "cuda")
 
+    def _operands(self, X, Y):
+        return _device_operand(X, self.x_extent, "X"), _device_operand(Y, self.y_extent, "Y")
+
     def execute(self, X, Y, workspace, stream=None):
-        _check(load_library().kron_varlen_execute(self.handle, X.data_ptr(), Y.data_ptr(), workspace.data_ptr(),
-                                                  workspace.numel(), _stream_handle(stream)),
+        xp, yp = self._operands(X, Y)
+        _check(load_library().kron_varlen_execute(self.handle, xp, yp, _device_operand(workspace, 0, "workspace"),
+                                                  workspace.numel() * workspace.element_size(),
+                                                  _stream_handle(stream)),
                "kron_varlen_execute")
         return Y
 
     def execute_noalloc(self, X, Y, stream=None):
         """Same result as execute(), with the library's fixed device array as the
         workspace (no allocation anywhere; at most 262,144 instances)."""
-        _check(load_library().kron_varlen_execute_noalloc(self.handle, X.data_ptr(), Y.data_ptr(),
-                                                          _stream_handle(stream)), "kron_varlen_execute_noalloc")
+        xp, yp = self._operands(X, Y)
+        _check(load_library().kron_varlen_execute_noalloc(self.handle, xp, yp, _stream_handle(stream)),
+               "kron_varlen_execute_noalloc")
         return Y
 
     def tune(self, X, Y, workspace, stream=None):
-        _check(load_library().kron_varlen_tune(self.handle, X.data_ptr(), Y.data_ptr(), workspace.data_ptr(),
-                                               workspace.numel(), _stream_handle(stream)), "kron_varlen_tune")
+        xp, yp = self._operands(X, Y)
+        _check(load_library().kron_varlen_tune(self.handle, xp, yp, _device_operand(workspace, 0, "workspace"),
+                                               workspace.numel() * workspace.element_size(),
+                                               _stream_handle(stream)), "kron_varlen_tune")
 
     def close(self):
         if getattr(self, "handle", None):

@@ -102,6 +102,41 @@ static bool ranges_overlap(const void* a, size_t abytes, const void* b, size_t b
     return a0 < b0 + bbytes && b0 < a0 + abytes;
 }
 
+}  // namespace kron
+
+// Whether [p, p + bytes) is device-accessible memory: a device or managed
+// allocation, the whole range inside it.  A host pointer or an extent beyond
+// the allocation would make a kernel fault, so the calls reject both before any
+// launch.  KRON_ERR_CUDA when the runtime cannot answer (no device).
+kron_status kron::device_range(const void* p, size_t bytes) {
+    cudaPointerAttributes at;
+    const cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return e == cudaErrorInvalidValue ? KRON_ERR_INVALID_VALUE : KRON_ERR_CUDA;
+    }
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) return KRON_ERR_INVALID_VALUE;
+    // The allocation's extent, from the driver (resolved once).
+    typedef int (*GetRange)(unsigned long long*, size_t*, unsigned long long);
+    static GetRange get_range = [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            fn = nullptr;
+        cudaGetLastError();
+        return reinterpret_cast<GetRange>(fn);
+    }();
+    if (!get_range) return KRON_OK;   // type check only
+    unsigned long long base = 0;
+    size_t size = 0;
+    if (get_range(&base, &size, (unsigned long long)(uintptr_t)p) != 0) return KRON_ERR_INVALID_VALUE;
+    return (uintptr_t)p + bytes <= base + size ? KRON_OK : KRON_ERR_INVALID_VALUE;
+}
+
+namespace kron {
+
 static void choose_yvec(KronDesc& d) {
     const size_t s = elem_size(d.io);
     d.yvec = 0;
@@ -175,6 +210,11 @@ KRON_API const char* kron_status_string(kron_status s) {
 
 KRON_API int kron_version(void) { return 10000; }
 
+KRON_API kron_status kron_check_device_buffer(const void* p, size_t bytes) {
+    if (!p) return KRON_ERR_INVALID_VALUE;
+    return device_range(p, bytes);
+}
+
 KRON_API kron_status kron2_batched(kron_stream_t stream, char transa, char transb, char transx, int ma, int na,
                                    int mb, int nb, int64_t batch_count, const void* alpha, const void* A, int lda,
                                    const void* B, int ldb, const void* X, int ldx, int64_t ldxp, const void* beta,
@@ -198,6 +238,7 @@ KRON_API kron_status kron2_batched(kron_stream_t stream, char transa, char trans
     const size_t xbytes = ((size_t)(batch_count - 1) * ldxp + (size_t)ldx * (xcols - 1) + xrows) * es;
     const size_t ybytes = ((size_t)(batch_count - 1) * ldyp + (size_t)ldy * (ma - 1) + mb) * es;
     if (ranges_overlap(X, xbytes, Y, ybytes)) return KRON_ERR_ALIAS;
+    if ((st = device_range(X, xbytes)) != KRON_OK || (st = device_range(Y, ybytes)) != KRON_OK) return st;
 
     static thread_local KronDesc d;
     d = KronDesc();
@@ -262,6 +303,7 @@ KRON_API kron_status kron_gemm_a_batched(kron_stream_t stream, char transa, char
     const size_t abytes = ((size_t)(batch_count - 1) * lda2 + aext) * es;
     const size_t cbytes = ((size_t)(batch_count - 1) * ldc2 + cext) * es;
     if (ranges_overlap(A, abytes, C, cbytes)) return KRON_ERR_ALIAS;
+    if ((st = device_range(A, abytes)) != KRON_OK || (st = device_range(C, cbytes)) != KRON_OK) return st;
     static thread_local GemmADesc g;
     g = GemmADesc();
     g.m = m;
@@ -305,6 +347,7 @@ KRON_API kron_status kron1_batched(kron_stream_t stream, char transa, int ma, in
     const size_t xbytes = ((size_t)(batch_count - 1) * ldxp + na) * es;
     const size_t ybytes = ((size_t)(batch_count - 1) * ldyp + ma) * es;
     if (ranges_overlap(X, xbytes, Y, ybytes)) return KRON_ERR_ALIAS;
+    if ((st = device_range(X, xbytes)) != KRON_OK || (st = device_range(Y, ybytes)) != KRON_OK) return st;
     // y^p (1 x ma) = x^p (1 x na) op(A)^T: TGEMM_A with m = 1, x^p as the one row
     // of A^p (column stride 1, instance stride ldxp) and the shared factor op(A)^T.
     static thread_local GemmADesc g;
@@ -357,6 +400,7 @@ KRON_API kron_status kron3_batched(kron_stream_t stream, char transa, char trans
     const size_t ybytes =
         ((size_t)(batch_count - 1) * ldyp + (size_t)ldy2 * (ma - 1) + (size_t)ldy * (mb - 1) + mc) * es;
     if (ranges_overlap(X, xbytes, Y, ybytes)) return KRON_ERR_ALIAS;
+    if ((st = device_range(X, xbytes)) != KRON_OK || (st = device_range(Y, ybytes)) != KRON_OK) return st;
 
     static thread_local KronDesc d;
     d = KronDesc();

@@ -42,6 +42,8 @@ struct KronDesc {
 };
 
 size_t elem_size(kron_dtype t);
+// KRON_OK when [p, p + bytes) lies inside one device or managed allocation.
+kron_status device_range(const void* p, size_t bytes);
 
 // Fills d.P / d.nstage from the tile-configuration table, if it has an entry.
 void apply_tile_config(KronDesc& d);

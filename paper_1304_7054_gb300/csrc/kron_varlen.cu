@@ -739,6 +739,10 @@ static kron_status vl_check_exec(kron_varlen_plan* plan, const void* X, void* Y,
     const uintptr_t w0 = (uintptr_t)workspace, w1 = w0 + plan->ws_bytes;
     if (x0 < y1 && y0 < x1) return KRON_ERR_ALIAS;
     if ((w0 < y1 && y0 < w1) || (w0 < x1 && x0 < w1)) return KRON_ERR_WORKSPACE;
+    kron_status st;
+    if ((st = device_range(X, plan->x_total * es)) != KRON_OK || (st = device_range(Y, plan->y_total * es)) != KRON_OK)
+        return st;
+    if ((st = device_range(workspace, plan->ws_bytes)) != KRON_OK) return st == KRON_ERR_CUDA ? st : KRON_ERR_WORKSPACE;
     return KRON_OK;
 }
 
@@ -840,6 +844,9 @@ KRON_API kron_status kron_varlen_execute_noalloc(kron_varlen_plan* plan, const v
     const uintptr_t y0 = (uintptr_t)Y, y1 = y0 + plan->y_total * es;
     if (x0 < y1 && y0 < x1) return KRON_ERR_ALIAS;
     if (plan->tiles.empty()) return KRON_OK;
+    kron_status rs;
+    if ((rs = device_range(X, plan->x_total * es)) != KRON_OK || (rs = device_range(Y, plan->y_total * es)) != KRON_OK)
+        return rs;
     const DeviceInfo& dev = device_info();
     if (dev.sms <= 0) return KRON_ERR_CUDA;
     if (plan->smem > dev.smem_per_block_optin) return KRON_ERR_NOT_SUPPORTED;

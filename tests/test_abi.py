@@ -143,3 +143,14 @@ def test_gemm_a_validation(lib, over, code):
         assert r not in (INVALID, NOTSUP, ALIAS)
     else:
         assert r == code
+
+
+def test_binding_rejects_cpu_tensors_without_a_gpu():
+    """A CPU tensor never reaches the library: its address would be a host pointer."""
+    import torch
+    n = 4
+    X = torch.zeros(2 * n * n)
+    with pytest.raises(TypeError):
+        kg.kron2_batched(np.eye(n), np.eye(n), X, X.clone(), ma=n, na=n, mb=n, nb=n, batch=2)
+    with pytest.raises(TypeError):
+        kg.kron1_batched(np.eye(n), X, X.clone(), ma=n, na=n, batch=2)
