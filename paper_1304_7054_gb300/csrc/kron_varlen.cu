@@ -13,15 +13,18 @@
 // (M[i,l], M[i+1,l]) and the operand duplicated), so each stage writes its
 // outputs as adjacent pairs; rows are padded to an even count.
 //
-// Data flow per CTA: two operand buffers.  While one tile is contracted, the
-// next one arrives in the other buffer by bulk copies, one per instance: an
-// instance starts anywhere (4-byte alignment for FP32), so each copy takes the
-// 16-byte-aligned span around it and the instance sits at its alignment phase
-// inside a 16-byte-aligned slot.  The last contraction writes each instance
-// contiguously into its slot (dead after the first contraction) at the phase of
-// its place in Y; the 16-byte-aligned middle leaves by one bulk copy and the at
-// most three elements on either side by plain stores.  Global memory is thus
-// read and written in whole aligned granules, with no per-element address work.
+// Data flow per CTA: two operand buffers and one exchange buffer.  While one
+// tile is contracted, the next one arrives in the other operand buffer by bulk
+// copies, one per instance: an instance starts anywhere (4-byte alignment for
+// FP32), so each copy takes the 16-byte-aligned span around it and the instance
+// sits at its alignment phase inside a 16-byte-aligned slot.  In 3-D the second
+// contraction writes over the dead operands and the last one into the exchange
+// buffer; in 2-D the last one writes over the dead operands.  Either way each
+// instance's results are contiguous, at the phase of its place in Y: the
+// 16-byte-aligned middle leaves by one bulk copy and the at most three elements
+// on either side by plain stores.  Global memory is thus read and written in
+// whole aligned granules, with no per-element address work.  Before the next
+// tile writes a buffer that outgoing copies still read, warp 0 waits for them.
 //
 // Workspace (caller-owned device memory, written on the first execute with a
 // given pointer): tile table (int4: class key, first sorted index, count, 0),
