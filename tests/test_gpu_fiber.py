@@ -266,3 +266,33 @@ def test_full_size_sampled(kind, n, batch, io):
     assert max_norm_err(got, ref, sub, Xs) <= TOL[io]
     del X, Y
     torch.cuda.empty_cache()
+
+
+# the other variants the benchmark times at full size: 16-bit storage (FP32 arithmetic)
+# and the odd-n in-place kernels, sampled instances against the FP64 oracle
+@pytest.mark.parametrize("kind,n,batch,io", [(2, 16, 1 << 20, "bf16"), (2, 16, 1 << 20, "f16"),
+                                             (2, 12, 1 << 20, "bf16"), (2, 12, 1 << 20, "f16"),
+                                             (2, 8, 1 << 20, "bf16"), (3, 16, 1 << 16, "bf16"),
+                                             (2, 15, 1 << 20, "f32"), (3, 15, 1 << 16, "f32")])
+def test_full_size_sampled_other_variants(kind, n, batch, io):
+    torch = _torch()
+    b = inputs.make_batch(kind, n, batch, seed=4, x_dist="normal", dtype=np.float32)
+    inst = n ** kind
+    xt, X64 = storage_x(b, io)
+    X = xt.to(torch_dtype(io)).cuda()
+    Y = torch.empty(batch * inst, dtype=torch_dtype(io), device="cuda")
+    if kind == 2:
+        kg.kron2_batched(b.A, b.B, X, Y, ma=n, na=n, mb=n, nb=n, batch=batch)
+    else:
+        kg.kron3_batched(b.A, b.B, b.C, X, Y, ma=n, na=n, mb=n, nb=n, mc=n, nc=n, batch=batch)
+    torch.cuda.synchronize()
+    assert kg.device_status() == 0
+    rng = np.random.default_rng(6)
+    idx = np.sort(rng.choice(batch, 2048, replace=False))
+    idx[-1] = batch - 1
+    Xs = X64.reshape(batch, inst)[idx].ravel()
+    sub = inputs.Batch(kind, n, len(idx), b.A, b.B, b.C, Xs)
+    got = Y.view(batch, inst)[torch.from_numpy(idx).cuda()].double().cpu().numpy().ravel()
+    assert max_norm_err(got, oracle_ref(sub, Xs), sub, Xs, io=io) <= TOL[io]
+    del X, Y
+    torch.cuda.empty_cache()
