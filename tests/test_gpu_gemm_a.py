@@ -227,3 +227,28 @@ def test_kron1_identity_is_exact():
     kg.kron1_batched(np.eye(16, dtype=np.float32), X, Y, ma=16, na=16, batch=5000)
     torch.cuda.synchronize()
     assert torch.equal(X, Y)
+
+
+def test_kron1_full_size_sampled():
+    """TKRON1 at the benchmark's launch: 2^24 vectors of n = 16, sampled instances."""
+    torch = _torch()
+    n, batch = 16, 1 << 24
+    rng = np.random.default_rng(21)
+    A1 = rng.uniform(-1, 1, (n, n)).astype(np.float32)
+    X = torch.randn(batch * n, device="cuda", generator=torch.Generator(device="cuda").manual_seed(3))
+    Y = torch.empty_like(X)
+    kg.kron1_batched(A1, X, Y, ma=n, na=n, batch=batch)
+    torch.cuda.synchronize()
+    assert kg.device_status() == 0
+    idx = np.sort(rng.choice(batch, 2048, replace=False))
+    idx[-1] = batch - 1
+    sel = torch.from_numpy(idx).cuda()
+    Xs = X.view(batch, n)[sel].double().cpu().numpy()
+    ref = oracle.kron1(np.ascontiguousarray(A1.T).ravel().astype(np.float64), Xs.ravel(), ma=n, na=n,
+                       batch=len(idx))
+    got = Y.view(batch, n)[sel].double().cpu().numpy().ravel()
+    err = (np.abs(got - ref).reshape(len(idx), n).max(axis=1) /
+           (np.linalg.norm(Xs, axis=1) * np.linalg.norm(A1.astype(np.float64)))).max()
+    assert err <= TOL["f32"]
+    del X, Y
+    torch.cuda.empty_cache()
