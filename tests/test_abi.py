@@ -154,3 +154,14 @@ def test_binding_rejects_cpu_tensors_without_a_gpu():
         kg.kron2_batched(np.eye(n), np.eye(n), X, X.clone(), ma=n, na=n, mb=n, nb=n, batch=2)
     with pytest.raises(TypeError):
         kg.kron1_batched(np.eye(n), X, X.clone(), ma=n, na=n, batch=2)
+
+
+def test_check_device_buffer_without_a_gpu():
+    """A null pointer is rejected outright; any other range needs the runtime,
+    which answers KRON_ERR_CUDA when no device is usable (a GPU run checks the
+    device cases)."""
+    import torch
+    assert kg.check_device_buffer(0, 16) == 1
+    if not torch.cuda.is_available():
+        h = np.zeros(4, np.float32)
+        assert kg.check_device_buffer(h.ctypes.data, h.nbytes) in (1, 5)
