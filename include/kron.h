@@ -95,9 +95,9 @@ KRON_API int kron_version(void);
 /*
  * kron_check_device_buffer -- the check every call makes on its X, Y (and
  * workspace) before launching: KRON_OK when [p, p + bytes) lies inside one
- * device or managed allocation of the current context.  KRON_ERR_INVALID_VALUE
- * for a null, host or unregistered pointer, or an extent past the end of the
- * allocation (such a launch would fault); KRON_ERR_CUDA when no device is
+ * device allocation of the current GPU or one managed allocation.  KRON_ERR_INVALID_VALUE
+ * for a null, host or unregistered pointer, memory of another GPU, or an extent
+ * past the end of the allocation (such a launch would fault); KRON_ERR_CUDA when no device is
  * usable.  Launches nothing.
  */
 KRON_API kron_status kron_check_device_buffer(const void* p, size_t bytes);

@@ -104,8 +104,8 @@ static bool ranges_overlap(const void* a, size_t abytes, const void* b, size_t b
 
 }  // namespace kron
 
-// Whether [p, p + bytes) is device-accessible memory: a device or managed
-// allocation, the whole range inside it.  A host pointer or an extent beyond
+// Whether [p, p + bytes) is device-accessible memory: a device allocation of
+// the current GPU or a managed allocation, the whole range inside it.  A host pointer or an extent beyond
 // the allocation would make a kernel fault, so the calls reject both before any
 // launch.  KRON_ERR_CUDA when the runtime cannot answer (no device).
 kron_status kron::device_range(const void* p, size_t bytes) {
@@ -116,6 +116,11 @@ kron_status kron::device_range(const void* p, size_t bytes) {
         return e == cudaErrorInvalidValue ? KRON_ERR_INVALID_VALUE : KRON_ERR_CUDA;
     }
     if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) return KRON_ERR_INVALID_VALUE;
+    if (at.type == cudaMemoryTypeDevice) {   // memory of another GPU: the launch runs on the current one
+        int cur = -1;
+        if (cudaGetDevice(&cur) != cudaSuccess) return KRON_ERR_CUDA;
+        if (at.device != cur) return KRON_ERR_INVALID_VALUE;
+    }
     // The allocation's extent, from the driver (resolved once).
     typedef int (*GetRange)(unsigned long long*, size_t*, unsigned long long);
     static GetRange get_range = [] {
