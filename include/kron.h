@@ -309,12 +309,16 @@ KRON_API kron_status kron_varlen_plan_destroy(kron_varlen_plan* plan);
  *  - It calls no cudaMalloc, cudaFree or other allocating routine, and launches
  *    the kernel directly (no graph).
  *  - The first call on a device looks up the array's device address with that
- *    device current.  Make that first call before any stream capture.
+ *    device current and keeps it for the life of the process.  After a
+ *    cudaDeviceReset that address is stale: do not call this entry point on a
+ *    device that has been reset since its first call.
  *  - Every call copies its tables into the array (a host-to-device copy from
- *    pageable memory; the call waits for it) and then launches.  Nothing is
- *    kept between calls.  All calls on a device share the one array, so calls
- *    whose work overlaps on the GPU (other streams, other host threads) race;
- *    serialise them.
+ *    pageable memory) and waits on `stream` for that copy before it launches.
+ *    Because each call synchronises its stream, it cannot be used while the
+ *    stream is being captured into a CUDA graph.  Nothing is kept between
+ *    calls.  All calls on a device share the one array, so calls whose work
+ *    overlaps on the GPU (other streams, other host threads) race; serialise
+ *    them.
  *  - Errors: as kron_varlen_execute (KRON_ERR_INVALID_VALUE, KRON_ERR_ALIAS,
  *    KRON_ERR_NOT_SUPPORTED, KRON_ERR_CUDA), plus KRON_ERR_WORKSPACE for a batch
  *    above the limit.

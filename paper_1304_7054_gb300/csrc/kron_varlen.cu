@@ -861,8 +861,7 @@ KRON_API kron_status kron_varlen_execute_noalloc(kron_varlen_plan* plan, const v
     r = vl_fill_args(plan, X, Y, ws);
     if (r != KRON_OK) return r;
     void* fn = vl_kernel_ptr(plan->io);
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan->smem) != cudaSuccess)
-        return KRON_ERR_CUDA;
+    if (!ensure_smem_optin(fn, plan->smem)) return KRON_ERR_CUDA;   // the attribute only ever grows
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kVlThreads, plan->smem) != cudaSuccess)
         return KRON_ERR_CUDA;
