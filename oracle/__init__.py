@@ -12,6 +12,10 @@ Three independent evaluations of the same operation (paper Sec. 2.1 / 2.2):
 * ``kron_matrix`` + ``matvec`` -- the explicit Kronecker matrix built from the
   block definition of Sec. 2, for tiny sizes.
 
+The complex field (Sec. 2) has its own entries with the same three forms:
+``kron2c`` / ``kron3c`` (op 'C' = Hermitian transpose, Sec. 2.2) and
+``kron_matrix_c`` + ``matvec_c``.
+
 It also holds the paper's two other interfaces of Sec. 3 as direct sums:
 ``kron1`` (TKRON1, the 1-D product, a batched GEMV with a shared matrix) and
 ``gemm_a`` (TGEMM_A, a batched GEMM whose first factor varies across the batch).
@@ -91,6 +95,20 @@ def bind(lib: ctypes.CDLL) -> ctypes.CDLL:
         fn = getattr(lib, "oracle_gemm_a_" + suf)
         fn.argtypes = [_C, _C, _I, _I, _I, scal, _P, _I, _L, _P, _I, scal, _P, _I, _L, _L]
         fn.restype = None
+    for suf in ("z", "c"):
+        for name in ("oracle_kron2_direct_", "oracle_kron2_factored_"):
+            fn = getattr(lib, name + suf)
+            fn.argtypes = [_C, _C, _C, _I, _I, _I, _I, _L, _P, _P, _I, _P, _I, _P, _I, _L, _P, _P, _I, _L]
+            fn.restype = None
+        for name in ("oracle_kron3_direct_", "oracle_kron3_factored_"):
+            fn = getattr(lib, name + suf)
+            fn.argtypes = [_C, _C, _C, _I, _I, _I, _I, _I, _I, _L, _P, _P, _I, _P, _I, _P, _I, _P, _I, _I, _L,
+                           _P, _P, _I, _I, _L]
+            fn.restype = None
+    lib.oracle_kron_matrix_z.argtypes = [_I, _I, _I, _I, _P, _I, _P, _I, _P]
+    lib.oracle_kron_matrix_z.restype = None
+    lib.oracle_matvec_z.argtypes = [_L, _L, _P, _P, _P]
+    lib.oracle_matvec_z.restype = None
     lib.oracle_kron_matrix_f64.argtypes = [_I, _I, _I, _I, _P, _I, _P, _I, _P]
     lib.oracle_kron_matrix_f64.restype = None
     lib.oracle_matvec_f64.argtypes = [_L, _L, _P, _P, _P]
@@ -255,6 +273,107 @@ def matvec(K, x, lib_override=None):
     y = np.zeros(rows, dtype=np.float64)
     L = lib_override or lib()
     L.oracle_matvec_f64(rows, cols, _ptr(Kf), _ptr(x), _ptr(y))
+    return y
+
+
+# ---------------------------------------------------------------------------
+# Complex entries: op in {'N', 'T', 'C'} ('C' = Hermitian transpose, Sec. 2.2);
+# precision "z" (complex128) or "c" (complex64); alpha, beta complex scalars.
+# ---------------------------------------------------------------------------
+def _cdt(precision: str):
+    if precision == "z":
+        return np.complex128, np.float64
+    if precision == "c":
+        return np.complex64, np.float32
+    raise ValueError(precision)
+
+
+def _scal(v, rdt):
+    v = complex(v)
+    return np.array([v.real, v.imag], dtype=rdt)
+
+
+def kron2c(A, B, X, *, ma, na, mb, nb, batch, lda=None, ldb=None, ldx=None, ldxp=None, ldy=None, ldyp=None,
+           alpha=1.0, beta=0.0, Y=None, transa="N", transb="N", transx="N", method="factored", precision="z",
+           lib_override=None):
+    """Complex Y^p <- alpha op(B) op(X^p) op(A)^T + beta Y^p (flat column-major buffers)."""
+    dt, rdt = _cdt(precision)
+    ta, tb, tx = (t.upper() for t in (transa, transb, transx))
+    lda = lda or (ma if ta == "N" else na)
+    ldb = ldb or (mb if tb == "N" else nb)
+    ldx = ldx or (nb if tx == "N" else na)
+    ldxp = ldx * (na if tx == "N" else nb) if ldxp is None else ldxp
+    ldy = ldy or mb
+    ldyp = ldy * ma if ldyp is None else ldyp
+    A = np.ascontiguousarray(A, dtype=dt).ravel()
+    B = np.ascontiguousarray(B, dtype=dt).ravel()
+    X = np.ascontiguousarray(X, dtype=dt).ravel()
+    if Y is None:
+        Y = np.zeros(max(1, (batch - 1) * ldyp + ldy * (ma - 1) + mb), dtype=dt)
+    else:
+        Y = np.array(Y, dtype=dt, copy=True).ravel()
+    al, be = _scal(alpha, rdt), _scal(beta, rdt)
+    L = lib_override or lib()
+    fn = getattr(L, f"oracle_kron2_{method}_{precision}")
+    fn(_b(ta), _b(tb), _b(tx), ma, na, mb, nb, batch, _ptr(al), _ptr(A), lda, _ptr(B), ldb, _ptr(X),
+       ldx, ldxp, _ptr(be), _ptr(Y), ldy, ldyp)
+    return Y
+
+
+def kron3c(A, B, C, X, *, ma, na, mb, nb, mc, nc, batch, lda=None, ldb=None, ldc=None, ldx=None, ldx2=None,
+           ldxp=None, ldy=None, ldy2=None, ldyp=None, alpha=1.0, beta=0.0, Y=None, transa="N", transb="N",
+           transc="N", method="factored", precision="z", lib_override=None):
+    """Complex Y^p[i,j,k] <- alpha sum op(C)[i,l] op(B)[j,m] op(A)[k,q] X^p[l,m,q] + beta Y^p."""
+    dt, rdt = _cdt(precision)
+    ta, tb, tc = (t.upper() for t in (transa, transb, transc))
+    lda = lda or (ma if ta == "N" else na)
+    ldb = ldb or (mb if tb == "N" else nb)
+    ldc = ldc or (mc if tc == "N" else nc)
+    ldx = ldx or nc
+    ldx2 = ldx2 or ldx * nb
+    ldxp = ldx2 * na if ldxp is None else ldxp
+    ldy = ldy or mc
+    ldy2 = ldy2 or ldy * mb
+    ldyp = ldy2 * ma if ldyp is None else ldyp
+    A = np.ascontiguousarray(A, dtype=dt).ravel()
+    B = np.ascontiguousarray(B, dtype=dt).ravel()
+    C = np.ascontiguousarray(C, dtype=dt).ravel()
+    X = np.ascontiguousarray(X, dtype=dt).ravel()
+    if Y is None:
+        Y = np.zeros(max(1, (batch - 1) * ldyp + ldy2 * (ma - 1) + ldy * (mb - 1) + mc), dtype=dt)
+    else:
+        Y = np.array(Y, dtype=dt, copy=True).ravel()
+    al, be = _scal(alpha, rdt), _scal(beta, rdt)
+    L = lib_override or lib()
+    fn = getattr(L, f"oracle_kron3_{method}_{precision}")
+    fn(_b(ta), _b(tb), _b(tc), ma, na, mb, nb, mc, nc, batch, _ptr(al), _ptr(A), lda, _ptr(B), ldb,
+       _ptr(C), ldc, _ptr(X), ldx, ldx2, ldxp, _ptr(be), _ptr(Y), ldy, ldy2, ldyp)
+    return Y
+
+
+def kron_matrix_c(A, B, lib_override=None):
+    """Explicit complex K = A (x) B (block definition, Sec. 2) for 2-D numpy arrays."""
+    A = np.asarray(A, dtype=np.complex128)
+    B = np.asarray(B, dtype=np.complex128)
+    ma, na = A.shape
+    mb, nb = B.shape
+    Af = np.ascontiguousarray(A.T).ravel()
+    Bf = np.ascontiguousarray(B.T).ravel()
+    K = np.zeros(ma * mb * na * nb, dtype=np.complex128)
+    L = lib_override or lib()
+    L.oracle_kron_matrix_z(ma, na, mb, nb, _ptr(Af), ma, _ptr(Bf), mb, _ptr(K))
+    return K.reshape(na * nb, ma * mb).T
+
+
+def matvec_c(K, x, lib_override=None):
+    """y = K x for a complex 2-D numpy array K, with the oracle's own loop."""
+    K = np.asarray(K, dtype=np.complex128)
+    rows, cols = K.shape
+    Kf = np.ascontiguousarray(K.T).ravel()
+    x = np.ascontiguousarray(x, dtype=np.complex128).ravel()
+    y = np.zeros(rows, dtype=np.complex128)
+    L = lib_override or lib()
+    L.oracle_matvec_z(rows, cols, _ptr(Kf), _ptr(x), _ptr(y))
     return y
 
 

@@ -34,6 +34,7 @@
  *
  * FP64 and FP32 variants; the FP32 variants accumulate in float and the file
  * is compiled with -ffp-contract=off so no fused multiply-add is formed.
+ * Complex variants of O1-O3 (op 'C' = Hermitian transpose) are at the end.
  */
 #include <stddef.h>
 #include <stdint.h>
@@ -259,4 +260,177 @@ ORACLE_API int oracle_num_threads(void)
 #else
     return 1;
 #endif
+}
+
+/* ===========================================================================
+ * Complex entries (the paper works over the complex field, Sec. 2, and its
+ * interfaces take T in {single, double} x {real, complex}, Sec. 3).
+ *
+ * op(M) is M, M^T or M^* (Hermitian transpose) for 'N', 'T' and 'C' (Sec. 2.2);
+ * op(X) of the 2-D case takes the same three values.  Storage is interleaved
+ * (real part, imaginary part), the layout of C99 complex types and numpy's
+ * complex64 / complex128.  alpha and beta are passed as pointers to their
+ * (real, imaginary) pair.  Suffix z = double complex, c = float complex; the
+ * arithmetic is C99 complex arithmetic, without fused multiply-adds.
+ * ======================================================================== */
+#include <complex.h>
+
+/* op(M)[r, c] for a column-major stored complex matrix, conjugated for 'C'. */
+#define ZOP(M, ld, t, r, c, CONJ)                                                             \
+    (((t) == 'N' || (t) == 'n') ? (M)[(size_t)(r) + (size_t)(ld) * (size_t)(c)]               \
+     : ((t) == 'T' || (t) == 't') ? (M)[(size_t)(c) + (size_t)(ld) * (size_t)(r)]             \
+     : CONJ((M)[(size_t)(c) + (size_t)(ld) * (size_t)(r)]))
+
+#define DEFINE_ORACLE_COMPLEX(T, R, SUF, CONJ)                                                 \
+/* O1, 2-D: Y[i,j] = alpha sum_l sum_m opB[i,l] opX[l,m] opA[j,m] + beta Y[i,j] */            \
+ORACLE_API void oracle_kron2_direct_##SUF(char ta, char tb, char tx, int ma, int na, int mb,   \
+    int nb, int64_t batch, const R* alpha_ri, const T* A, int lda, const T* B, int ldb,        \
+    const T* X, int ldx, int64_t ldxp, const R* beta_ri, T* Y, int ldy, int64_t ldyp)           \
+{                                                                                              \
+    const T al = alpha_ri[0] + alpha_ri[1] * I, be = beta_ri[0] + beta_ri[1] * I;              \
+    int64_t p;                                                                                 \
+    _Pragma("omp parallel for schedule(static)")                                               \
+    for (p = 0; p < batch; p++) {                                                              \
+        const T* Xc = X + p * ldxp;                                                            \
+        T* Yc = Y + p * ldyp;                                                                  \
+        for (int jj = 0; jj < ma; jj++)                                                        \
+            for (int ii = 0; ii < mb; ii++) {                                                  \
+                T acc = 0;                                                                     \
+                for (int ll = 0; ll < nb; ll++)                                                \
+                    for (int mm = 0; mm < na; mm++)                                            \
+                        acc += ZOP(B, ldb, tb, ii, ll, CONJ) * ZOP(Xc, ldx, tx, ll, mm, CONJ)  \
+                               * ZOP(A, lda, ta, jj, mm, CONJ);                                \
+                T* yo = &Yc[(size_t)ii + (size_t)ldy * jj];                                    \
+                *yo = (be == 0) ? al * acc : al * acc + be * *yo;                              \
+            }                                                                                  \
+    }                                                                                          \
+}                                                                                              \
+                                                                                               \
+/* O2, 2-D: Z = opB opX, then Y = alpha Z opA^T + beta Y (Algorithm 1's plane step). */      \
+ORACLE_API void oracle_kron2_factored_##SUF(char ta, char tb, char tx, int ma, int na, int mb, \
+    int nb, int64_t batch, const R* alpha_ri, const T* A, int lda, const T* B, int ldb,        \
+    const T* X, int ldx, int64_t ldxp, const R* beta_ri, T* Y, int ldy, int64_t ldyp)           \
+{                                                                                              \
+    const T al = alpha_ri[0] + alpha_ri[1] * I, be = beta_ri[0] + beta_ri[1] * I;              \
+    int64_t p;                                                                                 \
+    _Pragma("omp parallel for schedule(static)")                                               \
+    for (p = 0; p < batch; p++) {                                                              \
+        T W[16 * 16];                                                                          \
+        const T* Xc = X + p * ldxp;                                                            \
+        T* Yc = Y + p * ldyp;                                                                  \
+        for (int mm = 0; mm < na; mm++)                                                        \
+            for (int ii = 0; ii < mb; ii++) {                                                  \
+                T acc = 0;                                                                     \
+                for (int ll = 0; ll < nb; ll++)                                                \
+                    acc += ZOP(B, ldb, tb, ii, ll, CONJ) * ZOP(Xc, ldx, tx, ll, mm, CONJ);     \
+                W[ii + 16 * mm] = acc;                                                         \
+            }                                                                                  \
+        for (int jj = 0; jj < ma; jj++)                                                        \
+            for (int ii = 0; ii < mb; ii++) {                                                  \
+                T acc = 0;                                                                     \
+                for (int mm = 0; mm < na; mm++)                                                \
+                    acc += W[ii + 16 * mm] * ZOP(A, lda, ta, jj, mm, CONJ);                    \
+                T* yo = &Yc[(size_t)ii + (size_t)ldy * jj];                                    \
+                *yo = (be == 0) ? al * acc : al * acc + be * *yo;                              \
+            }                                                                                  \
+    }                                                                                          \
+}                                                                                              \
+                                                                                               \
+/* O1, 3-D: the triple sum of Sec. 2.1 (C on mode 1, B on mode 2, A on mode 3). */            \
+ORACLE_API void oracle_kron3_direct_##SUF(char ta, char tb, char tc, int ma, int na, int mb,   \
+    int nb, int mc, int nc, int64_t batch, const R* alpha_ri, const T* A, int lda, const T* B, \
+    int ldb, const T* C, int ldc, const T* X, int ldx, int ldx2, int64_t ldxp,                 \
+    const R* beta_ri, T* Y, int ldy, int ldy2, int64_t ldyp)                                   \
+{                                                                                              \
+    const T al = alpha_ri[0] + alpha_ri[1] * I, be = beta_ri[0] + beta_ri[1] * I;              \
+    int64_t p;                                                                                 \
+    _Pragma("omp parallel for schedule(static)")                                               \
+    for (p = 0; p < batch; p++) {                                                              \
+        const T* Xc = X + p * ldxp;                                                            \
+        T* Yc = Y + p * ldyp;                                                                  \
+        for (int kk = 0; kk < ma; kk++)                                                        \
+            for (int jj = 0; jj < mb; jj++)                                                    \
+                for (int ii = 0; ii < mc; ii++) {                                              \
+                    T acc = 0;                                                                 \
+                    for (int ll = 0; ll < nc; ll++)                                            \
+                        for (int mm = 0; mm < nb; mm++)                                        \
+                            for (int qq = 0; qq < na; qq++)                                    \
+                                acc += ZOP(C, ldc, tc, ii, ll, CONJ)                           \
+                                       * ZOP(B, ldb, tb, jj, mm, CONJ)                         \
+                                       * ZOP(A, lda, ta, kk, qq, CONJ)                         \
+                                       * Xc[(size_t)ll + (size_t)ldx * mm + (size_t)ldx2 * qq]; \
+                    T* yo = &Yc[(size_t)ii + (size_t)ldy * jj + (size_t)ldy2 * kk];            \
+                    *yo = (be == 0) ? al * acc : al * acc + be * *yo;                          \
+                }                                                                              \
+    }                                                                                          \
+}                                                                                              \
+                                                                                               \
+/* O2, 3-D, Algorithm 1: the 2-D step on every plane into tmp, then the third mode. */        \
+ORACLE_API void oracle_kron3_factored_##SUF(char ta, char tb, char tc, int ma, int na, int mb, \
+    int nb, int mc, int nc, int64_t batch, const R* alpha_ri, const T* A, int lda, const T* B, \
+    int ldb, const T* C, int ldc, const T* X, int ldx, int ldx2, int64_t ldxp,                 \
+    const R* beta_ri, T* Y, int ldy, int ldy2, int64_t ldyp)                                   \
+{                                                                                              \
+    const T al = alpha_ri[0] + alpha_ri[1] * I, be = beta_ri[0] + beta_ri[1] * I;              \
+    int64_t p;                                                                                 \
+    _Pragma("omp parallel for schedule(static)")                                               \
+    for (p = 0; p < batch; p++) {                                                              \
+        T W[16 * 16];                                                                          \
+        T tp[16 * 16 * 16];                                                                    \
+        const T* Xc = X + p * ldxp;                                                            \
+        T* Yc = Y + p * ldyp;                                                                  \
+        for (int qq = 0; qq < na; qq++) {                                                      \
+            const T* Xq = Xc + (size_t)ldx2 * qq;                                              \
+            for (int mm = 0; mm < nb; mm++)                                                    \
+                for (int ii = 0; ii < mc; ii++) {                                              \
+                    T acc = 0;                                                                 \
+                    for (int ll = 0; ll < nc; ll++)                                            \
+                        acc += ZOP(C, ldc, tc, ii, ll, CONJ) * Xq[(size_t)ll + (size_t)ldx * mm]; \
+                    W[ii + 16 * mm] = acc;                                                     \
+                }                                                                              \
+            for (int jj = 0; jj < mb; jj++)                                                    \
+                for (int ii = 0; ii < mc; ii++) {                                              \
+                    T acc = 0;                                                                 \
+                    for (int mm = 0; mm < nb; mm++)                                            \
+                        acc += W[ii + 16 * mm] * ZOP(B, ldb, tb, jj, mm, CONJ);                \
+                    tp[ii + 16 * jj + 256 * qq] = acc;                                         \
+                }                                                                              \
+        }                                                                                      \
+        for (int jj = 0; jj < mb; jj++)                                                        \
+            for (int kk = 0; kk < ma; kk++)                                                    \
+                for (int ii = 0; ii < mc; ii++) {                                              \
+                    T acc = 0;                                                                 \
+                    for (int qq = 0; qq < na; qq++)                                            \
+                        acc += tp[ii + 16 * jj + 256 * qq] * ZOP(A, lda, ta, kk, qq, CONJ);    \
+                    T* yo = &Yc[(size_t)ii + (size_t)ldy * jj + (size_t)ldy2 * kk];            \
+                    *yo = (be == 0) ? al * acc : al * acc + be * *yo;                          \
+                }                                                                              \
+    }                                                                                          \
+}
+
+DEFINE_ORACLE_COMPLEX(double complex, double, z, conj)
+DEFINE_ORACLE_COMPLEX(float complex, float, c, conjf)
+
+/* O3, complex: K = A (x) B from the block definition of Sec. 2 (no op()). */
+ORACLE_API void oracle_kron_matrix_z(int ma, int na, int mb, int nb, const double complex* A, int lda,
+                                     const double complex* B, int ldb, double complex* K)
+{
+    const size_t ldk = (size_t)ma * (size_t)mb;
+    for (int r = 0; r < ma; r++)
+        for (int c = 0; c < na; c++)
+            for (int i = 0; i < mb; i++)
+                for (int j = 0; j < nb; j++)
+                    K[((size_t)r * mb + i) + ldk * ((size_t)c * nb + j)] =
+                        A[(size_t)r + (size_t)lda * c] * B[(size_t)i + (size_t)ldb * j];
+}
+
+/* y = K x for a column-major complex (rows x cols) K. */
+ORACLE_API void oracle_matvec_z(int64_t rows, int64_t cols, const double complex* K, const double complex* x,
+                                double complex* y)
+{
+    for (int64_t r = 0; r < rows; r++) {
+        double complex s = 0;
+        for (int64_t c = 0; c < cols; c++) s += K[r + rows * c] * x[c];
+        y[r] = s;
+    }
 }
