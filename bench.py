@@ -58,16 +58,25 @@ WORKLOADS = {
     "kron3-bf16-n16": dict(kind=3, n=16, batch=1 << 16, io="bf16", compute="native", seed=4),
     "kron3-f64-n10": dict(kind=3, n=10, batch=1 << 18, io="f64", compute="native", seed=2),
     "kron2-f64-n10": dict(kind=2, n=10, batch=1 << 20, io="f64", compute="native", seed=1),
+    # complex storage (the paper's complex field, Sec. 2), interleaved
+    "kron2-c64-n16": dict(kind=2, n=16, batch=1 << 20, io="c64", compute="native", seed=6),
+    "kron3-c64-n16": dict(kind=3, n=16, batch=1 << 15, io="c64", compute="native", seed=6),
+    "kron2-c128-n16": dict(kind=2, n=16, batch=1 << 19, io="c128", compute="native", seed=6),
     # odd sizes (the mixed-size batch draws n from 4..16)
     "kron3-f32-n15": dict(kind=3, n=15, batch=1 << 16, io="f32", compute="native", seed=2),
     "kron2-f32-n15": dict(kind=2, n=15, batch=1 << 20, io="f32", compute="native", seed=1),
 }
 HEADLINE = "kron2-f32-n16"
-ESIZE = {"f32": 4, "f64": 8, "bf16": 2, "f16": 2}
+ESIZE = {"f32": 4, "f64": 8, "bf16": 2, "f16": 2, "c64": 8, "c128": 16}
+NP_DTYPE = {"f64": np.float64, "c64": np.complex64, "c128": np.complex128}
 
 
-def flops_per_instance(kind, n):
-    return 4 * n ** 3 if kind == 2 else 6 * n ** 4
+def flops_per_instance(kind, n, io="f32"):
+    """The paper's count (Sec. 5): 4 n^3 (2-D) or 6 n^4 (3-D) real flops per
+    instance.  A complex multiply-add is 8 real flops where a real one is 2, so
+    complex storage counts four times as many."""
+    f = 4 * n ** 3 if kind == 2 else 6 * n ** 4
+    return 4 * f if io in ("c64", "c128") else f
 
 
 def load_peaks():
@@ -174,7 +183,7 @@ def whole_job_rate(world, units_per_rank, ms):
 def make_inputs(wl, rank=0):
     from paper_1304_7054_gb300 import inputs
     b = inputs.make_batch(wl["kind"], wl["n"], wl["batch"], seed=rank_seed(wl["seed"], rank), x_dist="normal",
-                          dtype=np.float64 if wl["io"] == "f64" else np.float32)
+                          dtype=NP_DTYPE.get(wl["io"], np.float32))
     return b
 
 
@@ -201,22 +210,74 @@ def sample_error(kg, b, Y, io, torch):
     inst = b.n ** b.kind
     rng = np.random.default_rng(17)
     idx = np.sort(rng.choice(b.batch, min(512, b.batch), replace=False))
+    n = b.n
+    cplx = io in ("c64", "c128")
+    k2, k3 = (oracle.kron2c, oracle.kron3c) if cplx else (oracle.kron2, oracle.kron3)
     if io in ("bf16", "f16"):
         Xs = inputs.storage_to_f64(inputs.to_storage(b.X.reshape(b.batch, inst)[idx].ravel(), io))
     else:
-        Xs = b.X.reshape(b.batch, inst)[idx].astype(np.float64).ravel()
-    n = b.n
+        Xs = b.X.reshape(b.batch, inst)[idx].astype(np.complex128 if cplx else np.float64).ravel()
     if b.kind == 2:
-        ref = oracle.kron2(b.A, b.B, Xs, ma=n, na=n, mb=n, nb=n, batch=len(idx))
+        ref = k2(b.A, b.B, Xs, ma=n, na=n, mb=n, nb=n, batch=len(idx))
     else:
-        ref = oracle.kron3(b.A, b.B, b.C, Xs, ma=n, na=n, mb=n, nb=n, mc=n, nc=n, batch=len(idx))
-    got = Y.view(b.batch, inst)[torch.from_numpy(idx).to(Y.device)].double().cpu().numpy()
+        ref = k3(b.A, b.B, b.C, Xs, ma=n, na=n, mb=n, nb=n, mc=n, nc=n, batch=len(idx))
+    sel = Y.view(b.batch, inst)[torch.from_numpy(idx).to(Y.device)]
+    got = sel.cpu().numpy().astype(np.complex128) if cplx else sel.double().cpu().numpy()
     cn = 1.0
     for M in b.comps():
-        cn *= float(np.linalg.norm(np.asarray(M, np.float64)))
+        cn *= float(np.linalg.norm(np.asarray(M, np.complex128 if cplx else np.float64)))
     xn = np.linalg.norm(Xs.reshape(len(idx), inst), axis=1)
     d = np.abs(got - ref.reshape(len(idx), inst)).max(axis=1)
     return float((d / (cn * xn)).max())
+
+
+def storage_report(b, Y, io, torch, compute="native", samples=256):
+    """Accuracy of a 16-bit-storage result on seeded instances, against the FP64
+    oracle, in both readings of the error:
+      kernel: the oracle on the STORED operands.  A correct kernel computes each
+              output in FP32 (error at most E = kind * gamma_n * (|K| |x|)_i,
+              gamma_n = n u / (1 - n u), u = 2^-24; the split tensor path adds
+              3 * 2^-16 per contraction) and rounds it once to the storage type.
+              Reported: the fraction of outputs equal to the exact result rounded
+              to the storage type, and the largest |Y - y| / (1/2 ulp(|y| + E) + E),
+              which is <= 1 for a correct kernel.  (The FP32 value before the
+              rounding never leaves the kernel.)
+      end to end: the oracle on the original FP32 operands against the stored
+              result, normalised like the FP32 error (by ||A|| ||B|| (||C||) ||X^p||).
+    """
+    import oracle
+    from paper_1304_7054_gb300 import inputs
+    inst, n = b.n ** b.kind, b.n
+    rng = np.random.default_rng(19)
+    idx = np.sort(rng.choice(b.batch, min(samples, b.batch), replace=False))
+    X32 = b.X.reshape(b.batch, inst)[idx].ravel()
+    Xs = inputs.storage_to_f64(inputs.to_storage(X32, io))
+
+    def ref(X64, comps):
+        if b.kind == 2:
+            return oracle.kron2(comps[0], comps[1], X64, ma=n, na=n, mb=n, nb=n, batch=len(idx))
+        return oracle.kron3(comps[0], comps[1], comps[2], X64, ma=n, na=n, mb=n, nb=n, mc=n, nc=n,
+                            batch=len(idx))
+    comps = [np.asarray(M, np.float64) for M in b.comps()]
+    got = Y.view(b.batch, inst)[torch.from_numpy(idx).to(Y.device)].double().cpu().numpy().ravel()
+    y = ref(Xs, comps)
+    absref = ref(np.abs(Xs), [np.abs(M) for M in comps])
+    u = 2.0 ** -24
+    g = n * u / (1 - n * u)
+    factor = b.kind * (3 * 2.0 ** -16 + 2 * g) if compute == "bf16x3" else 1.01 * b.kind * g
+    E = factor * absref
+    p, emin = (8, -126) if io == "bf16" else (11, -14)
+    mag = np.abs(y) + E
+    e = np.where(mag > 0, np.maximum(np.floor(np.log2(np.where(mag > 0, mag, 1.0))), emin), emin)
+    allowed = 0.5 * np.ldexp(1.0, (e - (p - 1)).astype(np.int64)) + E
+    rounded = inputs.storage_to_f64(inputs.to_storage(y.astype(np.float32), io))
+    r_e2e = ref(X32.astype(np.float64), comps)
+    cn = float(np.prod([np.linalg.norm(M) for M in comps]))
+    xn = np.linalg.norm(X32.astype(np.float64).reshape(len(idx), inst), axis=1)
+    e2e = float((np.abs(got - r_e2e).reshape(len(idx), inst).max(axis=1) / (cn * xn)).max())
+    return {"instances": len(idx), "outputs_equal_to_rounded_exact": round(float(np.mean(got == rounded)), 6),
+            "max_excess_over_rounding_bar": round(float((np.abs(got - y) / allowed).max()), 4),
+            "end_to_end_max_norm_err_vs_fp32_operands": e2e}
 
 
 def time_device(kg, b, X, Y, compute, steps, warmup, torch, sampler=None, dist=None):
@@ -334,16 +395,51 @@ def measure_variant(kg, name, steps, warmup, torch, dev, peaks, tune=True):
         tile = kg.autotune(b.kind, b.n, b.batch, X, Y, compute=wl["compute"])
     total_ms, kern_ms = time_device(kg, b, X, Y, wl["compute"], steps, warmup, torch)
     err = sample_error(kg, b, Y, wl["io"], torch)
-    fl = flops_per_instance(b.kind, b.n) * b.batch
+    fl = flops_per_instance(b.kind, b.n, wl["io"]) * b.batch
     by = 2 * ESIZE[wl["io"]] * b.n ** b.kind * b.batch
     gbs = by / (kern_ms * 1e-3) / 1e9
     r = {"gflops": round(fl / (kern_ms * 1e-3) / 1e9, 1), "hbm_gbs": round(gbs, 1),
          "hbm_frac": round(gbs / peaks["hbm"], 4), "ms": round(kern_ms, 4), "batch": b.batch,
          "kernel": kernel_of(b.kind, b.n, wl["io"], wl["compute"]), "max_norm_err_vs_fp64_oracle": err,
          "tile": {"instances": tile[0], "pipeline_depth": tile[1]} if tile else None}
+    if wl["io"] in ("bf16", "f16"):
+        r["storage_rounding"] = storage_report(b, Y, wl["io"], torch, wl["compute"])
     del X, Y
     torch.cuda.empty_cache()
     return r
+
+
+ALU_ITERS = {"ffma2": 8192, "ffma": 8192, "dfma": 512}
+
+
+def measure_alu_peaks(kg, torch, dev, repeats=5):
+    """FMA throughput of the CUDA cores (the probe kernels of kron_peak_probe:
+    independent FMA chains on every SM), best of `repeats` launches timed with
+    CUDA events on the launching stream, with the SM clock sampled meanwhile."""
+    stream = torch.cuda.current_stream()
+    out = {}
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.2)
+    sampler.mark_on()
+    for unit, iters in ALU_ITERS.items():
+        kg.peak_probe(unit, iters)   # warm-up
+        best = None
+        for _ in range(repeats):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fl = kg.peak_probe(unit, iters)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None or ms < best else best
+        out[unit] = {"tflops": round(fl / (best * 1e-3) / 1e12, 2), "ms": round(best, 4)}
+    sampler.mark_off()
+    clocks = sampler.stop()
+    out["clocks"] = clocks
+    out["how"] = ("kron_peak_probe: 8 independent FMA chains per thread, 32 FMA instructions per loop trip, "
+                  "all resident CTAs on every SM; best of %d launches (CUDA events)" % repeats)
+    return out
 
 
 def _time_calls(fn, steps, warmup, torch):
@@ -440,6 +536,8 @@ def kernel_of(kind, n, io, compute):
     """Name of the kernel the library dispatches a contiguous batch to."""
     if compute == "bf16x3":
         return f"tc{kind}_kernel<n={n},{io}>"
+    if io in ("c64", "c128"):
+        return f"fiber_kernel<{io},n={n},{kind}-D>"
     if kind == 2 and n == 16 and io == "f32":
         return "pair16_kernel<f32,n=16,2-D>"
     if kind == 2 and n == 16 and io in ("bf16", "f16"):
@@ -607,7 +705,7 @@ def run_ours(args):
     total_ms = reduce_time_max(total_ms, dist, dev)
     err = sample_error(kg, b, Y, wl["io"], torch)
     ms = total_ms / args.steps
-    fl = flops_per_instance(b.kind, b.n) * b.batch
+    fl = flops_per_instance(b.kind, b.n, wl["io"]) * b.batch
     by = 2 * ESIZE[wl["io"]] * b.n ** b.kind * b.batch
     value = whole_job_rate(world, fl, ms) / 1e9
     kernel_name = kernel_of(b.kind, b.n, wl["io"], wl["compute"])
@@ -618,6 +716,7 @@ def run_ours(args):
     out = None
     if rank == 0:
         variants = {}
+        alu = measure_alu_peaks(kg, torch, dev)
         if not args.no_variants:
             for name in WORKLOADS:
                 if name != args.workload:
@@ -626,6 +725,12 @@ def run_ours(args):
                 variants[f"varlen-{io}"] = measure_varlen(kg, io, max(5, min(args.steps, 30)), 3, torch, dev,
                                                           peaks)
             variants.update(measure_interfaces(kg, max(5, min(args.steps, 30)), 3, torch, dev, peaks))
+        # share of the measured FMA throughput that the CUDA-core variants use
+        for name, r in variants.items():
+            w = WORKLOADS.get(name)
+            if w and "gflops" in r and w["compute"] == "native":
+                unit = {"f64": "dfma", "c128": "dfma", "c64": "ffma"}.get(w["io"], "ffma2")
+                r["of_measured_fma_peak"] = round(r["gflops"] / (alu[unit]["tflops"] * 1e3), 4)
         cpu = cpu_baseline(b, seconds=args.cpu_seconds)
         out = {
             "metric": METRIC, "value": round(value, 1), "unit": "GFlop/s", "n_gpus": world,
@@ -651,6 +756,7 @@ def run_ours(args):
                            "16 sub-batch calls on 3 streams overlap copies with compute"},
             "gpu_launches": args.steps,
             "clocks": clocks,
+            "alu_peaks_measured": alu,
             "variants": variants,
         }
         print(json.dumps(out), flush=True)
@@ -715,7 +821,7 @@ def run_profile(args):
     X = to_device_storage(b, wl["io"], torch, dev)
     Y = torch.empty_like(X)
     total_ms, kern_ms = time_device(kg, b, X, Y, wl["compute"], args.steps, args.warmup, torch)
-    fl = flops_per_instance(b.kind, b.n) * b.batch
+    fl = flops_per_instance(b.kind, b.n, wl["io"]) * b.batch
     by = 2 * ESIZE[wl["io"]] * b.n ** b.kind * b.batch
     print(json.dumps({"workload": args.workload, "batch": b.batch, "kernel_ms": kern_ms,
                       "gflops": fl / (kern_ms * 1e-3) / 1e9, "hbm_gbs": by / (kern_ms * 1e-3) / 1e9}))

@@ -29,9 +29,12 @@
  *    over the batch; Sec. 2.2 notes that transposing them once up front costs
  *    little, which is what the library does).  After the call returns the host
  *    arrays may be reused.  Type: float for KRON_R32F / KRON_R16BF / KRON_R16F
- *    storage, double for KRON_R64F.
+ *    storage, double for KRON_R64F, interleaved complex float / double pairs
+ *    for KRON_C32F / KRON_C64F (the complex field of Sec. 2).
  *  - alpha, beta: HOST pointers to scalars of the same type as the components.
  *    beta == 0 means Y is not read (NaN/Inf in Y are ignored, BLAS convention).
+ *  - trans arguments: 'N' = op(M) = M, 'T' = M^T, 'C' = M^H, the Hermitian
+ *    transpose (Sec. 2.2); for real storage 'C' is 'T'.
  *  - Leading dimensions are in elements (Sec. 3): ldx = column stride, ldx2 =
  *    plane stride (3-D), ldxp = offset between consecutive instances ("uniform
  *    offset from the previous entity").  ldxp may be 0 (one X for every p).
@@ -74,7 +77,9 @@ typedef enum {
     KRON_R32F = 0,   /* float;  components/alpha/beta float  */
     KRON_R64F = 1,   /* double; components/alpha/beta double */
     KRON_R16BF = 2,  /* bfloat16 operands, FP32 accumulation; components float */
-    KRON_R16F = 3    /* float16 operands, FP32 accumulation; components float */
+    KRON_R16F = 3,   /* float16 operands, FP32 accumulation; components float */
+    KRON_C32F = 4,   /* complex float, interleaved (re, im); components/alpha/beta complex float */
+    KRON_C64F = 5    /* complex double, interleaved (re, im); components/alpha/beta complex double */
 } kron_dtype;
 
 /* How the contractions are computed. */
@@ -94,11 +99,13 @@ KRON_API int kron_version(void);
 
 /*
  * kron_check_device_buffer -- the check every call makes on its X, Y (and
- * workspace) before launching: KRON_OK when [p, p + bytes) lies inside one
- * device allocation of the current GPU or one managed allocation.  KRON_ERR_INVALID_VALUE
- * for a null, host or unregistered pointer, memory of another GPU, or an extent
- * past the end of the allocation (such a launch would fault); KRON_ERR_CUDA when no device is
- * usable.  Launches nothing.
+ * workspace) before launching: KRON_OK when [p, p + bytes) is device memory of
+ * the current GPU or managed memory, mapped without a hole: one allocation, or
+ * adjacent mapped ranges (allocators that map memory in chunks through the
+ * virtual memory management API report one range per chunk).
+ * KRON_ERR_INVALID_VALUE for a null, host or unregistered pointer, memory of
+ * another GPU, or an extent past the end of the mapping (such a launch would
+ * fault); KRON_ERR_CUDA when no device is usable.  Launches nothing.
  */
 KRON_API kron_status kron_check_device_buffer(const void* p, size_t bytes);
 
@@ -112,7 +119,11 @@ KRON_API kron_status kron_check_device_buffer(const void* p, size_t bytes);
  *          (ldx >= nb if transx = 'N', >= na if 'T')
  *   Y^p:   mb x ma at Y + p*ldyp, column stride ldy >= mb,
  *          ldyp >= ldy*(ma-1) + mb (instances of Y must not overlap)
- *   trans*: 'N'/'n' = no transpose, 'T'/'t' = transpose ('C'/'c' = 'T' for real data)
+ *   trans*: 'N'/'n' = no transpose, 'T'/'t' = transpose, 'C'/'c' = Hermitian
+ *          transpose (= 'T' for real data); transx = 'C' conjugates X^p
+ *
+ * Complex storage (KRON_C32F, KRON_C64F) runs on the CUDA cores
+ * (KRON_COMPUTE_NATIVE; the split tensor path is for real data).
  *
  * Errors: KRON_ERR_INVALID_VALUE (bad size, ld, trans, null pointer with
  * batch_count > 0, negative batch or stride), KRON_ERR_NOT_SUPPORTED (compute
@@ -162,8 +173,9 @@ KRON_API kron_status kron3_batched(kron_stream_t stream, char transa, char trans
  *
  * The paper prints both vector strides under one name; they are read as the X
  * and the Y stride.  alpha, beta: host scalars of the compute type; beta = 0
- * means Y is not read.  Storage: any kron_dtype; compute: KRON_COMPUTE_NATIVE
- * only (KRON_ERR_NOT_SUPPORTED otherwise).  Errors: KRON_ERR_INVALID_VALUE
+ * means Y is not read.  Storage: any real kron_dtype (complex storage returns
+ * KRON_ERR_NOT_SUPPORTED); compute: KRON_COMPUTE_NATIVE only
+ * (KRON_ERR_NOT_SUPPORTED otherwise).  Errors: KRON_ERR_INVALID_VALUE
  * (bad size, ld, stride, trans, null pointer with batch_count > 0),
  * KRON_ERR_ALIAS (X and Y ranges overlap), KRON_ERR_CUDA.  batch_count = 0 is a
  * no-op.  It runs on the kron_gemm_a_batched kernel with m = 1.
@@ -191,8 +203,8 @@ KRON_API kron_status kron1_batched(kron_stream_t stream, char transa, int ma, in
  *
  * The paper uses it for the third mode of its 3-D algorithm (Algorithm 1):
  * with tmp^p the (mc mb) x na result of the 2-D product on every plane,
- * Y^p = tmp^p op(A)^T.  Storage: any kron_dtype; compute: KRON_COMPUTE_NATIVE
- * only.  Errors as kron1_batched (KRON_ERR_ALIAS when the A and C ranges
+ * Y^p = tmp^p op(A)^T.  Storage: any real kron_dtype (complex storage returns
+ * KRON_ERR_NOT_SUPPORTED); compute: KRON_COMPUTE_NATIVE only.  Errors as kron1_batched (KRON_ERR_ALIAS when the A and C ranges
  * overlap).
  */
 KRON_API kron_status kron_gemm_a_batched(kron_stream_t stream, char transa, char transb, int m, int n, int k,
@@ -208,6 +220,37 @@ KRON_API kron_status kron_gemm_a_batched(kron_stream_t stream, char transa, char
  * call (its outputs for that launch are then incomplete), or KRON_ERR_CUDA.
  */
 KRON_API kron_status kron_device_status(kron_stream_t stream);
+
+/*
+ * kron_set_first_wait_limit_ns -- a test aid for the failure path, off by
+ * default (0).  With ns > 0, the first operand wait of every CTA of later
+ * launches of the 2-D n = 16 FP32 kernel (kron2_batched, contiguous FP32
+ * batches, n = 16) polls for at most ns nanoseconds instead of the normal
+ * limit.  A limit shorter than an operand copy takes to land makes that real
+ * wait expire on a normal launch: the kernel records the expiry in the device
+ * status word (kron_device_status then returns KRON_ERR_DEVICE_TIMEOUT), waits
+ * with the normal bound for its copies still in flight, and returns; the
+ * outputs of that launch are incomplete.  Every other wait keeps the normal
+ * limit (2 s).  Process-wide.  Errors: KRON_ERR_INVALID_VALUE for ns above the
+ * normal limit.
+ */
+KRON_API kron_status kron_set_first_wait_limit_ns(unsigned long long ns);
+
+/*
+ * kron_peak_probe -- a measurement aid with no computation of the operation:
+ * the roofline of the CUDA-core contraction kernels is the FMA throughput the
+ * chip sustains (the paper quotes its GPU's peaks from the data sheet, Sec. 5;
+ * here they are measured).  Launches one kernel on `stream` that runs only
+ * independent FMA chains, with operands in registers, on every SM, and returns
+ * in *flops the floating-point operations of that launch (2 per FMA).  The
+ * caller times the launch (CUDA events on `stream`).
+ *   unit 0: FP32, packed two-lane fma.rn.f32x2 (the form the FP32 kernels use)
+ *   unit 1: FP32, scalar fma.rn.f32
+ *   unit 2: FP64, fma.rn.f64
+ * iters: loop trips, 1 .. 2^24; each trip is 32 FMA instructions per thread.
+ * Errors: KRON_ERR_INVALID_VALUE (unit, iters or flops), KRON_ERR_CUDA (launch).
+ */
+KRON_API kron_status kron_peak_probe(kron_stream_t stream, int unit, int iters, double* flops);
 
 /*
  * Tile configuration of the fixed-size kernels, per (kind, n, io, comp):

@@ -24,7 +24,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libkron_gb300.so")
 KRON_OK = 0
 STATUS = {0: "KRON_OK", 1: "KRON_ERR_INVALID_VALUE", 2: "KRON_ERR_NOT_SUPPORTED", 3: "KRON_ERR_ALIAS",
           4: "KRON_ERR_WORKSPACE", 5: "KRON_ERR_CUDA", 6: "KRON_ERR_DEVICE_TIMEOUT"}
-DTYPES = {"f32": 0, "f64": 1, "bf16": 2, "f16": 3}
+DTYPES = {"f32": 0, "f64": 1, "bf16": 2, "f16": 3, "c64": 4, "c128": 5}
 COMPUTE = {"native": 0, "bf16x3": 1}
 
 # Every entry point declared in include/kron.h, with its ctypes signature.
@@ -41,6 +41,8 @@ SIGNATURES = {
     "kron_gemm_a_batched": ([_P, _C, _C, _I, _I, _I, _P, _P, _I, _L, _P, _I, _P, _P, _I, _L, _L, _I, _I, _I],
                             _I),
     "kron_device_status": ([_P], _I),
+    "kron_set_first_wait_limit_ns": ([ctypes.c_ulonglong], _I),
+    "kron_peak_probe": ([_P, _I, _I, ctypes.POINTER(ctypes.c_double)], _I),
     "kron_set_tile_config": ([_I, _I, _I, _I, _I, _I], _I),
     "kron_get_tile_config": ([_I, _I, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
     "kron_autotune": ([_P, _I, _I, _L, _P, _P, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
@@ -93,7 +95,8 @@ def _torch():
 
 def _io_of(t) -> int:
     torch = _torch()
-    m = {torch.float32: "f32", torch.float64: "f64", torch.bfloat16: "bf16", torch.float16: "f16"}
+    m = {torch.float32: "f32", torch.float64: "f64", torch.bfloat16: "bf16", torch.float16: "f16",
+         torch.complex64: "c64", torch.complex128: "c128"}
     if t.dtype not in m:
         raise TypeError(f"unsupported storage dtype {t.dtype}")
     return DTYPES[m[t.dtype]]
@@ -129,7 +132,16 @@ def _device_operand(t, need, name):
 
 
 def _scalar(v, ctype):
+    """A host scalar of the compute type; complex scalars as their (re, im) pair."""
+    if ctype in (np.complex64, np.complex128):
+        v = complex(v)
+        return ((ctypes.c_double if ctype == np.complex128 else ctypes.c_float) * 2)(v.real, v.imag)
     return (ctypes.c_double if ctype == np.float64 else ctypes.c_float)(v)
+
+
+def _ctype_of(io):
+    """Host type of the components, alpha and beta for storage type io."""
+    return {DTYPES["f64"]: np.float64, DTYPES["c64"]: np.complex64, DTYPES["c128"]: np.complex128}.get(io, np.float32)
 
 
 def kron2_batched(A, B, X, Y, *, ma, na, mb, nb, batch, alpha=1.0, beta=0.0, transa="N", transb="N",
@@ -141,7 +153,7 @@ def kron2_batched(A, B, X, Y, *, ma, na, mb, nb, batch, alpha=1.0, beta=0.0, tra
     io = _io_of(X)
     if _io_of(Y) != io:
         raise TypeError("X and Y must have the same dtype")
-    ctype = np.float64 if io == DTYPES["f64"] else np.float32
+    ctype = _ctype_of(io)
     Ab, lda0 = _comp_buffer(A, ctype)
     Bb, ldb0 = _comp_buffer(B, ctype)
     ta, tb, tx = transa.upper(), transb.upper(), transx.upper()
@@ -170,7 +182,7 @@ def kron3_batched(A, B, C, X, Y, *, ma, na, mb, nb, mc, nc, batch, alpha=1.0, be
     io = _io_of(X)
     if _io_of(Y) != io:
         raise TypeError("X and Y must have the same dtype")
-    ctype = np.float64 if io == DTYPES["f64"] else np.float32
+    ctype = _ctype_of(io)
     Ab, lda0 = _comp_buffer(A, ctype)
     Bb, ldb0 = _comp_buffer(B, ctype)
     Cb, ldc0 = _comp_buffer(C, ctype)
@@ -202,7 +214,7 @@ def kron1_batched(A, X, Y, *, ma, na, batch, alpha=1.0, beta=0.0, transa="N", ld
     io = _io_of(X)
     if _io_of(Y) != io:
         raise TypeError("X and Y must have the same dtype")
-    ctype = np.float64 if io == DTYPES["f64"] else np.float32
+    ctype = _ctype_of(io)
     Ab, lda0 = _comp_buffer(A, ctype)
     ta = transa.upper()
     lda = lda or lda0 or (ma if ta == "N" else na)
@@ -224,7 +236,7 @@ def gemm_a_batched(A, B, C, *, m, n, k, batch, alpha=1.0, beta=0.0, transa="N", 
     io = _io_of(A)
     if _io_of(C) != io:
         raise TypeError("A and C must have the same dtype")
-    ctype = np.float64 if io == DTYPES["f64"] else np.float32
+    ctype = _ctype_of(io)
     Bb, ldb0 = _comp_buffer(B, ctype)
     ta, tb = transa.upper(), transb.upper()
     lda = lda or (m if ta == "N" else k)
@@ -255,6 +267,24 @@ def check_device_buffer(t, nbytes=None) -> int:
 def device_status(stream=None) -> int:
     """Synchronise and read/clear the device status word (0 = OK)."""
     return load_library().kron_device_status(_stream_handle(stream))
+
+
+def set_first_wait_limit_ns(ns: int) -> None:
+    """Failure-path test aid: the first operand wait of each CTA of the 2-D n = 16
+    FP32 kernel polls for at most ns nanoseconds (0 restores the normal limit)."""
+    _check(load_library().kron_set_first_wait_limit_ns(ns), "kron_set_first_wait_limit_ns")
+
+
+PEAK_UNITS = {"ffma2": 0, "ffma": 1, "dfma": 2}
+
+
+def peak_probe(unit, iters, stream=None) -> float:
+    """Launch the FMA-throughput probe of `unit` ("ffma2", "ffma", "dfma") on the
+    stream; returns the flops of that launch (the caller times it)."""
+    f = ctypes.c_double()
+    _check(load_library().kron_peak_probe(_stream_handle(stream), PEAK_UNITS[unit], iters, ctypes.byref(f)),
+           "kron_peak_probe")
+    return f.value
 
 
 def set_tile_config(kind, n, io, compute="native", instances_per_tile=0, pipeline_depth=0):

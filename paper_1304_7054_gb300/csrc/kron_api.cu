@@ -3,6 +3,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <utility>
@@ -21,9 +22,13 @@ size_t elem_size(kron_dtype t) {
         case KRON_R64F: return 8;
         case KRON_R16BF:
         case KRON_R16F: return 2;
+        case KRON_C32F: return 8;
+        case KRON_C64F: return 16;
     }
     return 0;
 }
+
+bool is_complex(kron_dtype t) { return t == KRON_C32F || t == KRON_C64F; }
 
 constexpr int kMaxDevices = 64;
 
@@ -76,6 +81,10 @@ unsigned* device_error_word() {
     return ptr[dev];
 }
 
+static std::atomic<unsigned long long> g_first_wait_ns{0};
+
+unsigned long long first_wait_limit_ns() { return g_first_wait_ns.load(std::memory_order_relaxed); }
+
 static bool trans_flag(char t, int* is_t) {
     switch (t) {
         case 'N': case 'n': *is_t = 0; return true;
@@ -83,6 +92,9 @@ static bool trans_flag(char t, int* is_t) {
         default: return false;
     }
 }
+
+// 'C' / 'c' (Hermitian transpose) conjugates complex data.
+static int conj_flag(char t, kron_dtype io) { return is_complex(io) && (t == 'C' || t == 'c'); }
 
 static bool dim_ok(int v) { return v >= 1 && v <= kMaxN; }
 
@@ -97,6 +109,33 @@ static void op_pad(double* out, int N, const void* M, int ld, int is_t, int rows
         }
 }
 
+// Complex op(M) (rows x cols), conjugated for 'C', zero-padded into N x N
+// real and imaginary parts.  M holds interleaved (re, im) pairs.
+static void op_pad_complex(double* re, double* im, int N, const void* M, int ld, int is_t, int conj, int rows,
+                           int cols, bool dbl) {
+    for (int e = 0; e < N * N; ++e) re[e] = im[e] = 0.0;
+    for (int c = 0; c < cols; ++c)
+        for (int r = 0; r < rows; ++r) {
+            const size_t idx = is_t ? (size_t)c + (size_t)ld * r : (size_t)r + (size_t)ld * c;
+            const double vr = dbl ? static_cast<const double*>(M)[2 * idx] : (double)static_cast<const float*>(M)[2 * idx];
+            const double vi =
+                dbl ? static_cast<const double*>(M)[2 * idx + 1] : (double)static_cast<const float*>(M)[2 * idx + 1];
+            re[r + N * c] = vr;
+            im[r + N * c] = conj ? -vi : vi;
+        }
+}
+
+// A host scalar of the compute type of io: (re, im) for complex storage.
+static void scalar_of(const void* v, kron_dtype io, double* re, double* im) {
+    *im = 0.0;
+    switch (io) {
+        case KRON_R64F: *re = *static_cast<const double*>(v); break;
+        case KRON_C64F: *re = static_cast<const double*>(v)[0]; *im = static_cast<const double*>(v)[1]; break;
+        case KRON_C32F: *re = static_cast<const float*>(v)[0]; *im = static_cast<const float*>(v)[1]; break;
+        default: *re = (double)*static_cast<const float*>(v); break;
+    }
+}
+
 static bool ranges_overlap(const void* a, size_t abytes, const void* b, size_t bbytes) {
     const uintptr_t a0 = (uintptr_t)a, b0 = (uintptr_t)b;
     return a0 < b0 + bbytes && b0 < a0 + abytes;
@@ -104,11 +143,9 @@ static bool ranges_overlap(const void* a, size_t abytes, const void* b, size_t b
 
 }  // namespace kron
 
-// Whether [p, p + bytes) is device-accessible memory: a device allocation of
-// the current GPU or a managed allocation, the whole range inside it.  A host pointer or an extent beyond
-// the allocation would make a kernel fault, so the calls reject both before any
-// launch.  KRON_ERR_CUDA when the runtime cannot answer (no device).
-kron_status kron::device_range(const void* p, size_t bytes) {
+// Whether address p is device-accessible memory: a device allocation of the
+// current GPU or a managed allocation.
+static kron_status device_pointer(const void* p) {
     cudaPointerAttributes at;
     const cudaError_t e = cudaPointerGetAttributes(&at, p);
     if (e != cudaSuccess) {
@@ -121,6 +158,20 @@ kron_status kron::device_range(const void* p, size_t bytes) {
         if (cudaGetDevice(&cur) != cudaSuccess) return KRON_ERR_CUDA;
         if (at.device != cur) return KRON_ERR_INVALID_VALUE;
     }
+    return KRON_OK;
+}
+
+// Whether [p, p + bytes) is device-accessible memory of the current GPU (device
+// or managed), mapped without a hole.  A host pointer or an extent beyond the
+// mapping would make a kernel fault, so the calls reject both before any launch.
+// The driver reports one mapped range per query; allocators that map memory in
+// chunks (virtual memory management, e.g. expandable segments) give one range
+// per chunk, so the check walks adjacent ranges, each of which must itself be
+// device memory of this GPU.  KRON_ERR_CUDA when the runtime cannot answer (no
+// device).
+kron_status kron::device_range(const void* p, size_t bytes) {
+    kron_status st = device_pointer(p);
+    if (st != KRON_OK) return st;
     // The allocation's extent, from the driver (resolved once).
     typedef int (*GetRange)(unsigned long long*, size_t*, unsigned long long);
     static GetRange get_range = [] {
@@ -134,10 +185,17 @@ kron_status kron::device_range(const void* p, size_t bytes) {
         return reinterpret_cast<GetRange>(fn);
     }();
     if (!get_range) return KRON_OK;   // type check only
-    unsigned long long base = 0;
-    size_t size = 0;
-    if (get_range(&base, &size, (unsigned long long)(uintptr_t)p) != 0) return KRON_ERR_INVALID_VALUE;
-    return (uintptr_t)p + bytes <= base + size ? KRON_OK : KRON_ERR_INVALID_VALUE;
+    const unsigned long long end = (unsigned long long)(uintptr_t)p + bytes;
+    unsigned long long cur = (unsigned long long)(uintptr_t)p;
+    for (int seg = 0; seg < 65536; ++seg) {
+        unsigned long long base = 0;
+        size_t size = 0;
+        if (get_range(&base, &size, cur) != 0 || size == 0 || base + size <= cur) return KRON_ERR_INVALID_VALUE;
+        if (end <= base + size) return KRON_OK;
+        cur = base + size;   // first byte after this range: mapped device memory of this GPU, or the end
+        if ((st = device_pointer((const void*)(uintptr_t)cur)) != KRON_OK) return st;
+    }
+    return KRON_ERR_INVALID_VALUE;
 }
 
 namespace kron {
@@ -156,6 +214,8 @@ static void choose_yvec(KronDesc& d) {
 
 static kron_status dispatch(KronDesc& d, cudaStream_t st) {
     apply_tile_config(d);
+    if (d.io == KRON_C32F) return d.D == 2 ? launch_fiber_c32_d2(d, st) : launch_fiber_c32_d3(d, st);
+    if (d.io == KRON_C64F) return d.D == 2 ? launch_fiber_c64_d2(d, st) : launch_fiber_c64_d3(d, st);
     if (d.comp == KRON_COMPUTE_32F_BF16X3) return launch_tc(d, st);
     if (d.contiguous && d.ycontig && d.N % 2 == 0 && d.io != KRON_R64F) {
         kron_status r = KRON_ERR_NOT_SUPPORTED;
@@ -188,8 +248,10 @@ static kron_status dispatch(KronDesc& d, cudaStream_t st) {
 }
 
 static kron_status check_modes(kron_dtype io, kron_compute comp) {
-    if (io != KRON_R32F && io != KRON_R64F && io != KRON_R16BF && io != KRON_R16F) return KRON_ERR_INVALID_VALUE;
+    if (io != KRON_R32F && io != KRON_R64F && io != KRON_R16BF && io != KRON_R16F && !is_complex(io))
+        return KRON_ERR_INVALID_VALUE;
     if (comp == KRON_COMPUTE_NATIVE) return KRON_OK;
+    if (is_complex(io)) return comp == KRON_COMPUTE_32F_BF16X3 ? KRON_ERR_NOT_SUPPORTED : KRON_ERR_INVALID_VALUE;
     if (comp == KRON_COMPUTE_32F_BF16X3) return (io == KRON_R32F || io == KRON_R16BF) ? KRON_OK : KRON_ERR_NOT_SUPPORTED;
     return KRON_ERR_INVALID_VALUE;
 }
@@ -247,11 +309,16 @@ KRON_API kron_status kron2_batched(kron_stream_t stream, char transa, char trans
 
     static thread_local KronDesc d;
     d = KronDesc();
-    const bool dbl = io == KRON_R64F;
+    const bool dbl = io == KRON_R64F || io == KRON_C64F;
     d.D = 2;
     d.N = std::max(std::max(ma, na), std::max(mb, nb));
-    op_pad(d.m1, d.N, B, ldb, tb, mb, nb, dbl);
-    op_pad(d.m2, d.N, A, lda, ta, ma, na, dbl);
+    if (is_complex(io)) {
+        op_pad_complex(d.m1, d.m1i, d.N, B, ldb, tb, conj_flag(transb, io), mb, nb, dbl);
+        op_pad_complex(d.m2, d.m2i, d.N, A, lda, ta, conj_flag(transa, io), ma, na, dbl);
+    } else {
+        op_pad(d.m1, d.N, B, ldb, tb, mb, nb, dbl);
+        op_pad(d.m2, d.N, A, lda, ta, ma, na, dbl);
+    }
     memset(d.m3, 0, sizeof(d.m3));
     d.X = X;
     d.Y = Y;
@@ -263,14 +330,15 @@ KRON_API kron_status kron2_batched(kron_stream_t stream, char transa, char trans
     d.ldx2 = 0;
     d.ldy2 = 0;
     d.transx = tx;
+    d.conjx = conj_flag(transx, io);
     d.xe[0] = nb; d.xe[1] = na; d.xe[2] = 1;
     d.ye[0] = mb; d.ye[1] = ma; d.ye[2] = 1;
-    d.alpha = dbl ? *static_cast<const double*>(alpha) : (double)*static_cast<const float*>(alpha);
-    d.beta = dbl ? *static_cast<const double*>(beta) : (double)*static_cast<const float*>(beta);
+    scalar_of(alpha, io, &d.alpha, &d.alpha_im);
+    scalar_of(beta, io, &d.beta, &d.beta_im);
     d.io = io;
     d.comp = comp;
     const int N = d.N;
-    d.contiguous = ma == N && na == N && mb == N && nb == N && !tx && ldx == N && ldxp == (int64_t)N * N &&
+    d.contiguous = ma == N && na == N && mb == N && nb == N && !tx && !d.conjx && ldx == N && ldxp == (int64_t)N * N &&
                    ((uintptr_t)X) % 16 == 0;
     d.ycontig = d.contiguous && ldy == N && ldyp == (int64_t)N * N && ((uintptr_t)Y) % 16 == 0;
     choose_yvec(d);
@@ -295,7 +363,7 @@ KRON_API kron_status kron_gemm_a_batched(kron_stream_t stream, char transa, char
     if (batch_count < 0 || grid_size < 0 || lda2 < 0 || ldc2 < 0) return KRON_ERR_INVALID_VALUE;
     kron_status st = check_modes(io, comp);
     if (st != KRON_OK) return st;
-    if (comp != KRON_COMPUTE_NATIVE) return KRON_ERR_NOT_SUPPORTED;
+    if (comp != KRON_COMPUTE_NATIVE || is_complex(io)) return KRON_ERR_NOT_SUPPORTED;
     if (lda < (ta ? k : m) || ldb < (tb ? n : k) || ldc < m) return KRON_ERR_INVALID_VALUE;
     const int64_t cext = (int64_t)ldc * (n - 1) + m;   // elements spanned by one C^p
     if (batch_count > 1 && ldc2 < cext) return KRON_ERR_INVALID_VALUE;   // instances of C may not overlap
@@ -341,7 +409,7 @@ KRON_API kron_status kron1_batched(kron_stream_t stream, char transa, int ma, in
     if (batch_count < 0 || ldxp < 0 || ldyp < 0) return KRON_ERR_INVALID_VALUE;
     kron_status st = check_modes(io, comp);
     if (st != KRON_OK) return st;
-    if (comp != KRON_COMPUTE_NATIVE) return KRON_ERR_NOT_SUPPORTED;
+    if (comp != KRON_COMPUTE_NATIVE || is_complex(io)) return KRON_ERR_NOT_SUPPORTED;
     if (lda < (ta ? na : ma)) return KRON_ERR_INVALID_VALUE;
     if (batch_count > 1 && ldyp < ma) return KRON_ERR_INVALID_VALUE;   // outputs may not overlap
     if (!alpha || !beta) return KRON_ERR_INVALID_VALUE;
@@ -409,12 +477,18 @@ KRON_API kron_status kron3_batched(kron_stream_t stream, char transa, char trans
 
     static thread_local KronDesc d;
     d = KronDesc();
-    const bool dbl = io == KRON_R64F;
+    const bool dbl = io == KRON_R64F || io == KRON_C64F;
     d.D = 3;
     d.N = std::max(std::max(std::max(ma, na), std::max(mb, nb)), std::max(mc, nc));
-    op_pad(d.m1, d.N, C, ldc, tc, mc, nc, dbl);
-    op_pad(d.m2, d.N, B, ldb, tb, mb, nb, dbl);
-    op_pad(d.m3, d.N, A, lda, ta, ma, na, dbl);
+    if (is_complex(io)) {
+        op_pad_complex(d.m1, d.m1i, d.N, C, ldc, tc, conj_flag(transc, io), mc, nc, dbl);
+        op_pad_complex(d.m2, d.m2i, d.N, B, ldb, tb, conj_flag(transb, io), mb, nb, dbl);
+        op_pad_complex(d.m3, d.m3i, d.N, A, lda, ta, conj_flag(transa, io), ma, na, dbl);
+    } else {
+        op_pad(d.m1, d.N, C, ldc, tc, mc, nc, dbl);
+        op_pad(d.m2, d.N, B, ldb, tb, mb, nb, dbl);
+        op_pad(d.m3, d.N, A, lda, ta, ma, na, dbl);
+    }
     d.X = X;
     d.Y = Y;
     d.batch = batch_count;
@@ -427,8 +501,8 @@ KRON_API kron_status kron3_batched(kron_stream_t stream, char transa, char trans
     d.transx = 0;
     d.xe[0] = nc; d.xe[1] = nb; d.xe[2] = na;
     d.ye[0] = mc; d.ye[1] = mb; d.ye[2] = ma;
-    d.alpha = dbl ? *static_cast<const double*>(alpha) : (double)*static_cast<const float*>(alpha);
-    d.beta = dbl ? *static_cast<const double*>(beta) : (double)*static_cast<const float*>(beta);
+    scalar_of(alpha, io, &d.alpha, &d.alpha_im);
+    scalar_of(beta, io, &d.beta, &d.beta_im);
     d.io = io;
     d.comp = comp;
     const int N = d.N;
@@ -437,6 +511,12 @@ KRON_API kron_status kron3_batched(kron_stream_t stream, char transa, char trans
     d.ycontig = d.contiguous && ldy == N && ldy2 == N * N && ldyp == (int64_t)N * N * N && ((uintptr_t)Y) % 16 == 0;
     choose_yvec(d);
     return dispatch(d, (cudaStream_t)stream);
+}
+
+KRON_API kron_status kron_set_first_wait_limit_ns(unsigned long long ns) {
+    if (ns > kWaitLimitNs) return KRON_ERR_INVALID_VALUE;
+    g_first_wait_ns.store(ns, std::memory_order_relaxed);
+    return KRON_OK;
 }
 
 KRON_API kron_status kron_device_status(kron_stream_t stream) {

@@ -88,6 +88,35 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
     }
 }
 
+// Non-blocking test of phase `parity` of `bar`.
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Waits for phase `parity` of `bar` by polling (no suspension), for at most
+// limit_ns of %globaltimer.  On expiry it records kDevErrTimeout in *err and
+// returns false.  Used with a short limit to make a real wait run out (the
+// failure-path test of kron_set_first_wait_limit_ns).
+__device__ __forceinline__ bool mbar_wait_polled(uint64_t* bar, unsigned parity, unsigned* err,
+                                                 unsigned long long limit_ns) {
+    const unsigned long long t0 = global_timer_ns();
+    for (;;) {
+        if (mbar_test(bar, parity)) return true;
+        if (global_timer_ns() - t0 >= limit_ns) {
+            atomicOr(err, kDevErrTimeout);
+            return false;
+        }
+    }
+}
+
 // L2 policy for data read exactly once (the operand stream).
 __device__ __forceinline__ uint64_t l2_evict_first_policy() {
     uint64_t pol;

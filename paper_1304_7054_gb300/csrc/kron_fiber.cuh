@@ -25,10 +25,17 @@
 // (Sec. 5 attributes the 3-D slowdown to it); here it never leaves the SM.
 #pragma once
 
+#include "kron_complex.cuh"
 #include "kron_device.cuh"
 #include "kron_internal.h"
 
 namespace kron {
+
+// Storage <-> compute for complex storage (the compute type is the same).
+template <> __device__ __forceinline__ cf32 load_cvt<cf32, cf32>(cf32 v) { return v; }
+template <> __device__ __forceinline__ cf64 load_cvt<cf64, cf64>(cf64 v) { return v; }
+template <> __device__ __forceinline__ cf32 store_cvt<cf32, cf32>(cf32 v) { return v; }
+template <> __device__ __forceinline__ cf64 store_cvt<cf64, cf64>(cf64 v) { return v; }
 
 template <typename T, int N, int D>
 struct FiberArgs {
@@ -42,6 +49,7 @@ struct FiberArgs {
     int xe1, xe2, xe3;            // extents of op(X); entries beyond are read as 0
     int ye1, ye2, ye3;            // extents of Y; entries beyond are not written
     int transx;
+    int conjx;                    // complex storage: op(X) conjugates (transx = 'C')
     int P;                        // instances per tile
     int nstage;                   // bulk-copy pipeline depth (0: generic loads)
     int yvec;                     // Y store chunk bytes (16/8/4) or 0 (elements)
@@ -74,7 +82,7 @@ __device__ __forceinline__ void contract(const T* __restrict__ M, const T (&x)[N
 #pragma unroll
     for (int l = 1; l < N; ++l) {
 #pragma unroll
-        for (int i = 0; i < N; ++i) y[i] = fma(M[i + N * l], x[l], y[i]);
+        for (int i = 0; i < N; ++i) y[i] = madd(M[i + N * l], x[l], y[i]);
     }
 }
 
@@ -137,6 +145,8 @@ __device__ __forceinline__ void load_tile_generic(const FiberArgs<T, N, D>& a, S
             else
                 off += i1 + (int64_t)a.ldx * i2 + (int64_t)a.ldx2 * i3;
             v = X[off];
+            if constexpr (is_cplx<S>::value)
+                if (a.conjx) v = conj_of(v);
         }
         xt[e] = v;
     }
@@ -153,10 +163,29 @@ __device__ __forceinline__ void store_fiber(const FiberArgs<T, N, D>& a, S* dst,
 #pragma unroll
         for (int i = 0; i < N; ++i) {
             const T old = (i < a.ye1) ? load_cvt<T, S>(dst[i]) : T(0);
-            o[i] = store_cvt<S, T>(fma(a.alpha, y[i], a.beta * old));
+            o[i] = store_cvt<S, T>(madd(a.alpha, y[i], a.beta * old));
         }
     }
-    if constexpr (sizeof(S) == 8) {
+    if constexpr (is_cplx<S>::value) {
+        // 16-byte vector stores: one complex double, or two complex floats
+        if (a.yvec == 16) {
+            if constexpr (sizeof(S) == 16) {
+#pragma unroll
+                for (int i = 0; i < N; ++i) __stcs(reinterpret_cast<double2*>(dst) + i, make_double2(o[i].re, o[i].im));
+                return;
+            } else if constexpr (N % 2 == 0) {
+#pragma unroll
+                for (int c = 0; c < N / 2; ++c)
+                    __stcs(reinterpret_cast<float4*>(dst) + c,
+                           make_float4(o[2 * c].re, o[2 * c].im, o[2 * c + 1].re, o[2 * c + 1].im));
+                return;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+            if (i < a.ye1) dst[i] = o[i];
+        return;
+    } else if constexpr (sizeof(S) == 8) {
         if (a.yvec == 16) {
 #pragma unroll
             for (int c = 0; c < N / 2; ++c)
@@ -347,10 +376,18 @@ kron_status launch_fiber_n(const KronDesc& d, cudaStream_t st) {
     const DeviceInfo& dev = device_info();
     if (dev.sms <= 0) return KRON_ERR_CUDA;
     FiberArgs<T, N, D> a;
+    auto elem = [](double re, double im) -> T {
+        if constexpr (is_cplx<T>::value) {
+            using R = decltype(T().re);
+            return T(static_cast<R>(re), static_cast<R>(im));
+        } else {
+            return static_cast<T>(re);
+        }
+    };
     for (int e = 0; e < N * N; ++e) {
-        a.m1[e] = static_cast<T>(d.m1[e]);
-        a.m2[e] = static_cast<T>(d.m2[e]);
-        if constexpr (D == 3) a.m3[e] = static_cast<T>(d.m3[e]);
+        a.m1[e] = elem(d.m1[e], d.m1i[e]);
+        a.m2[e] = elem(d.m2[e], d.m2i[e]);
+        if constexpr (D == 3) a.m3[e] = elem(d.m3[e], d.m3i[e]);
     }
     if constexpr (D == 2) a.m3[0] = T(0);
     a.X = d.X;
@@ -365,11 +402,12 @@ kron_status launch_fiber_n(const KronDesc& d, cudaStream_t st) {
     a.xe1 = d.xe[0]; a.xe2 = d.xe[1]; a.xe3 = d.xe[2];
     a.ye1 = d.ye[0]; a.ye2 = d.ye[1]; a.ye3 = d.ye[2];
     a.transx = d.transx;
+    a.conjx = d.conjx;
     a.yvec = d.yvec;
-    a.alpha = static_cast<T>(d.alpha);
-    a.beta = static_cast<T>(d.beta);
-    a.beta_zero = d.beta == 0.0;
-    a.alpha_one = d.alpha == 1.0;
+    a.alpha = elem(d.alpha, d.alpha_im);
+    a.beta = elem(d.beta, d.beta_im);
+    a.beta_zero = d.beta == 0.0 && d.beta_im == 0.0;
+    a.alpha_one = d.alpha == 1.0 && d.alpha_im == 0.0;
     a.err = device_error_word();
     if (!a.err) return KRON_ERR_CUDA;
 

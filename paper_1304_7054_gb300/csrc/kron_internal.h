@@ -21,6 +21,10 @@ struct KronDesc {
     double m1[kMaxN * kMaxN];
     double m2[kMaxN * kMaxN];
     double m3[kMaxN * kMaxN];
+    // imaginary parts (complex storage; zero otherwise)
+    double m1i[kMaxN * kMaxN] = {};
+    double m2i[kMaxN * kMaxN] = {};
+    double m3i[kMaxN * kMaxN] = {};
     const void* X = nullptr;
     void* Y = nullptr;
     int64_t batch = 0, ldxp = 0, ldyp = 0;
@@ -28,7 +32,9 @@ struct KronDesc {
     int xe[3] = {1, 1, 1};   // extents of op(X) per mode
     int ye[3] = {1, 1, 1};   // extents of Y per mode
     int transx = 0;
+    int conjx = 0;      // complex: op(X) is the Hermitian transpose
     double alpha = 1.0, beta = 0.0;
+    double alpha_im = 0.0, beta_im = 0.0;
     kron_dtype io = KRON_R32F;
     kron_compute comp = KRON_COMPUTE_NATIVE;
     // derived by the dispatcher
@@ -42,6 +48,7 @@ struct KronDesc {
 };
 
 size_t elem_size(kron_dtype t);
+bool is_complex(kron_dtype t);
 // KRON_OK when [p, p + bytes) lies inside one device or managed allocation.
 kron_status device_range(const void* p, size_t bytes);
 
@@ -57,6 +64,8 @@ constexpr size_t kVarlenNoallocScratchBytes = (size_t)8 << 20;
 
 // Device status word of the current device (device pointer).
 unsigned* device_error_word();
+// Limit of the first operand wait set by kron_set_first_wait_limit_ns (0 = off).
+unsigned long long first_wait_limit_ns();
 
 // CUDA-core (fiber) kernels, one entry per storage type and kind (one
 // translation unit each, so they compile in parallel).
@@ -68,6 +77,10 @@ kron_status launch_fiber_bf16_d2(const KronDesc& d, cudaStream_t s);
 kron_status launch_fiber_bf16_d3(const KronDesc& d, cudaStream_t s);
 kron_status launch_fiber_f16_d2(const KronDesc& d, cudaStream_t s);
 kron_status launch_fiber_f16_d3(const KronDesc& d, cudaStream_t s);
+kron_status launch_fiber_c32_d2(const KronDesc& d, cudaStream_t s);
+kron_status launch_fiber_c32_d3(const KronDesc& d, cudaStream_t s);
+kron_status launch_fiber_c64_d2(const KronDesc& d, cudaStream_t s);
+kron_status launch_fiber_c64_d3(const KronDesc& d, cudaStream_t s);
 
 // Packed-pair FP32 kernels (even N, contiguous X and Y); KRON_ERR_NOT_SUPPORTED
 // for shapes they do not handle.

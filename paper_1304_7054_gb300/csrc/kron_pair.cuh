@@ -110,6 +110,9 @@ struct PairArgs {
     int beta_zero, alpha_one;
     float alpha, beta;
     unsigned* err;
+    // Nonzero: the first operand wait of each CTA polls for at most this many
+    // nanoseconds (failure-path test; read by the 2-D n = 16 FP32 kernel).
+    unsigned long long first_wait_ns = 0;
 };
 
 template <int N, int D, int SB>

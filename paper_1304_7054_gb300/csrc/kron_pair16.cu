@@ -124,7 +124,9 @@ __global__ void __launch_bounds__(kThreads, 6) pair16_kernel(const __grid_consta
         float* buf = ring + s * kTileWords;
         const int64_t inst0 = tile * kTileP;
         const int cnt = (int)min((int64_t)kTileP, a.batch - inst0);
-        const bool ok = mbar_wait_bounded(&full[s], (unsigned)(it / NB) & 1u, a.err);
+        const bool ok = (it == 0 && a.first_wait_ns)
+                            ? mbar_wait_polled(&full[s], 0u, a.err, a.first_wait_ns)
+                            : mbar_wait_bounded(&full[s], (unsigned)(it / NB) & 1u, a.err);
 
         // Stage 1: rows (l, l+1) of instance q times M2^T, written back in place.
         {
@@ -358,6 +360,7 @@ kron_status launch_pair16(const KronDesc& d, cudaStream_t st) {
     a.alpha_one = d.alpha == 1.0;
     a.err = device_error_word();
     if (!a.err) return KRON_ERR_CUDA;
+    a.first_wait_ns = d.io == KRON_R32F ? first_wait_limit_ns() : 0;
     a.P = kTileP;
     // FP32: one buffer per CTA (measured best: the six to seven resident CTAs
     // per SM overlap one another's copies; a second buffer costs resident CTAs).

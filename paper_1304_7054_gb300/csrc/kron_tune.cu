@@ -125,14 +125,17 @@ KRON_API kron_status kron_autotune(kron_stream_t stream, int kind, int n, int64_
     if ((kind != 2 && kind != 3) || n < 1 || n > kMaxN || batch_count < 1 || !X || !Y) return KRON_ERR_INVALID_VALUE;
     cudaStream_t st = (cudaStream_t)stream;
     // Components do not change the timing; identity keeps the outputs finite.
-    double eye[kMaxN * kMaxN] = {};
-    float eyef[kMaxN * kMaxN] = {};
-    for (int i = 0; i < n; ++i) eye[i + n * i] = eyef[i + n * i] = 1.0f;
-    const void* comp_ptr = io == KRON_R64F ? (const void*)eye : (const void*)eyef;
-    const double one = 1.0, zero = 0.0;
-    const float onef = 1.0f, zerof = 0.0f;
-    const void* al = io == KRON_R64F ? (const void*)&one : (const void*)&onef;
-    const void* be = io == KRON_R64F ? (const void*)&zero : (const void*)&zerof;
+    // Buffers hold (re, im) pairs so that they also serve complex storage.
+    const bool dbl = io == KRON_R64F || io == KRON_C64F;
+    const int w = is_complex(io) ? 2 : 1;
+    double eye[2 * kMaxN * kMaxN] = {};
+    float eyef[2 * kMaxN * kMaxN] = {};
+    for (int i = 0; i < n; ++i) eye[w * (i + n * i)] = eyef[w * (i + n * i)] = 1.0f;
+    const void* comp_ptr = dbl ? (const void*)eye : (const void*)eyef;
+    const double one[2] = {1.0, 0.0}, zero[2] = {0.0, 0.0};
+    const float onef[2] = {1.0f, 0.0f}, zerof[2] = {0.0f, 0.0f};
+    const void* al = dbl ? (const void*)one : (const void*)onef;
+    const void* be = dbl ? (const void*)zero : (const void*)zerof;
     auto run = [&]() -> kron_status {
         if (kind == 2)
             return kron2_batched(stream, 'N', 'N', 'N', n, n, n, n, batch_count, al, comp_ptr, n, comp_ptr, n, X, n,

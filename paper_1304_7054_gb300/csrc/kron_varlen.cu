@@ -633,7 +633,7 @@ KRON_API kron_status kron_varlen_plan_create(kron_varlen_plan** plan, int num_cl
     if (num_classes > 0 && !classes) return KRON_ERR_INVALID_VALUE;
     if (batch_count > 0 && (!h_class_of || !h_x_off || !h_y_off)) return KRON_ERR_INVALID_VALUE;
     if (io != KRON_R32F && io != KRON_R16BF && io != KRON_R16F) {
-        return (io == KRON_R64F) ? KRON_ERR_NOT_SUPPORTED : KRON_ERR_INVALID_VALUE;
+        return (io == KRON_R64F || is_complex(io)) ? KRON_ERR_NOT_SUPPORTED : KRON_ERR_INVALID_VALUE;
     }
     if (comp != KRON_COMPUTE_NATIVE) return comp == KRON_COMPUTE_32F_BF16X3 ? KRON_ERR_NOT_SUPPORTED
                                                                             : KRON_ERR_INVALID_VALUE;

@@ -10,7 +10,9 @@ finite-element operands:
 * components ~ U[-1, 1], drawn in the order A, B, C (C only for 3-D);
 * operands X^p ~ U[-1, 1] (``x_dist="uniform"``) or N(0, 1) (``"normal"``),
   drawn after the components, batch-major, column-major inside an instance;
-* generator: numpy PCG64 (``numpy.random.default_rng(seed)``).
+* generator: numpy PCG64 (``numpy.random.default_rng(seed)``);
+* complex data (``dtype`` complex64 / complex128): every array draws its real
+  parts, then its imaginary parts, from the same distribution.
 """
 from __future__ import annotations
 
@@ -39,7 +41,28 @@ class Batch:
         return (self.A, self.B) if self.kind == 2 else (self.A, self.B, self.C)
 
 
+def _is_complex(dtype):
+    return np.dtype(dtype).kind == "c"
+
+
+def _real_of(dtype):
+    return np.float64 if np.dtype(dtype) == np.complex128 else np.float32
+
+
+def _uniform(rng, size, dtype):
+    if _is_complex(dtype):
+        r = rng.uniform(-1.0, 1.0, size)
+        return (r + 1j * rng.uniform(-1.0, 1.0, size)).astype(dtype)
+    return rng.uniform(-1.0, 1.0, size).astype(dtype)
+
+
 def _draw_x(rng, size, x_dist, dtype):
+    if _is_complex(dtype):
+        re = _draw_x(rng, size, x_dist, _real_of(dtype))
+        im = _draw_x(rng, size, x_dist, _real_of(dtype))
+        out = np.empty(size, dtype=dtype)
+        out.real, out.imag = re, im
+        return out
     if x_dist == "uniform":
         return rng.uniform(-1.0, 1.0, size).astype(dtype)
     if x_dist == "normal":
@@ -53,9 +76,9 @@ def make_batch(kind: int, n: int, batch: int, seed: int, x_dist: str = "normal",
                dtype=np.float32) -> Batch:
     """Components then operands from one PCG64 stream (draw order A, B, C, X)."""
     rng = np.random.default_rng(seed)
-    A = rng.uniform(-1.0, 1.0, n * n).astype(dtype)
-    B = rng.uniform(-1.0, 1.0, n * n).astype(dtype)
-    C = rng.uniform(-1.0, 1.0, n * n).astype(dtype) if kind == 3 else None
+    A = _uniform(rng, n * n, dtype)
+    B = _uniform(rng, n * n, dtype)
+    C = _uniform(rng, n * n, dtype) if kind == 3 else None
     X = _draw_x(rng, batch * n ** kind, x_dist, dtype)
     return Batch(kind, n, batch, A, B, C, X, seed, x_dist)
 

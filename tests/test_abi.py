@@ -74,7 +74,8 @@ INVALID, NOTSUP, ALIAS = 1, 2, 3
     (dict(ldy=3), INVALID), (dict(ldyp=15), INVALID), (dict(ldxp=-1), INVALID),
     (dict(alpha=None), INVALID), (dict(beta=None), INVALID), (dict(X=None), INVALID), (dict(Y=None), INVALID),
     (dict(A=None), INVALID), (dict(io=7), INVALID), (dict(comp=9), INVALID),
-    (dict(io=1, comp=1), NOTSUP), (dict(io=3, comp=1), NOTSUP),
+    (dict(io=1, comp=1), NOTSUP), (dict(io=3, comp=1), NOTSUP), (dict(io=4, comp=1), NOTSUP),
+    (dict(io=5, comp=1), NOTSUP), (dict(io=6), INVALID),
     (dict(Y=0x10000 + 4 * 100), ALIAS), (dict(X=0x90000), ALIAS),
     (dict(X=0x10002), INVALID),            # not aligned to the element size
     (dict(ta=b"T", lda=3, ma=3, na=4), INVALID),   # stored A is na x ma: lda >= na
@@ -165,3 +166,16 @@ def test_check_device_buffer_without_a_gpu():
     if not torch.cuda.is_available():
         h = np.zeros(4, np.float32)
         assert kg.check_device_buffer(h.ctypes.data, h.nbytes) in (1, 5)
+
+
+def test_first_wait_limit_is_validated(lib):
+    assert lib.kron_set_first_wait_limit_ns(10 ** 12) == INVALID   # above the normal 2 s limit
+    assert lib.kron_set_first_wait_limit_ns(5) == 0
+    assert lib.kron_set_first_wait_limit_ns(0) == 0
+
+
+def test_peak_probe_rejects_bad_arguments(lib):
+    f = ctypes.c_double()
+    assert lib.kron_peak_probe(None, 3, 10, ctypes.byref(f)) == INVALID
+    assert lib.kron_peak_probe(None, 0, 0, ctypes.byref(f)) == INVALID
+    assert lib.kron_peak_probe(None, 0, 10, None) == INVALID
