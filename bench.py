@@ -391,8 +391,8 @@ def measure_variant(kg, name, steps, warmup, torch, dev, peaks, tune=True):
     except kg.KronError as e:
         return {"unavailable": str(e)}
     tile = None
-    if tune:   # the library's autotuner picks the tile size and pipeline depth (untimed)
-        tile = kg.autotune(b.kind, b.n, b.batch, X, Y, compute=wl["compute"])
+    if tune:   # the library's autotuner picks body, tile, pipeline depth, fibers per step (untimed)
+        tile = kg.autotune_config(b.kind, b.n, b.batch, X, Y, compute=wl["compute"])
     total_ms, kern_ms = time_device(kg, b, X, Y, wl["compute"], steps, warmup, torch)
     err = sample_error(kg, b, Y, wl["io"], torch)
     fl = flops_per_instance(b.kind, b.n, wl["io"]) * b.batch
@@ -400,8 +400,9 @@ def measure_variant(kg, name, steps, warmup, torch, dev, peaks, tune=True):
     gbs = by / (kern_ms * 1e-3) / 1e9
     r = {"gflops": round(fl / (kern_ms * 1e-3) / 1e9, 1), "hbm_gbs": round(gbs, 1),
          "hbm_frac": round(gbs / peaks["hbm"], 4), "ms": round(kern_ms, 4), "batch": b.batch,
-         "kernel": kernel_of(b.kind, b.n, wl["io"], wl["compute"]), "max_norm_err_vs_fp64_oracle": err,
-         "tile": {"instances": tile[0], "pipeline_depth": tile[1]} if tile else None}
+         "kernel": kernel_of(b.kind, b.n, wl["io"], wl["compute"], (tile or {}).get("variant", "auto")),
+         "max_norm_err_vs_fp64_oracle": err,
+         "tuned_config": tile}
     if wl["io"] in ("bf16", "f16"):
         r["storage_rounding"] = storage_report(b, Y, wl["io"], torch, wl["compute"])
     del X, Y
@@ -532,12 +533,15 @@ def measure_interfaces(kg, steps, warmup, torch, dev, peaks):
     return out
 
 
-def kernel_of(kind, n, io, compute):
-    """Name of the kernel the library dispatches a contiguous batch to."""
+def kernel_of(kind, n, io, compute, variant="auto"):
+    """Name of the kernel the library dispatches a contiguous batch to (with the
+    kernel body the tuning table holds for it)."""
     if compute == "bf16x3":
         return f"tc{kind}_kernel<n={n},{io}>"
-    if io in ("c64", "c128"):
+    if io in ("c64", "c128") or variant == "scalar":
         return f"fiber_kernel<{io},n={n},{kind}-D>"
+    if variant == "exchange":
+        return f"pair_kernel<{io},n={n},{kind}-D>"
     if kind == 2 and n == 16 and io == "f32":
         return "pair16_kernel<f32,n=16,2-D>"
     if kind == 2 and n == 16 and io in ("bf16", "f16"):

@@ -282,6 +282,60 @@ KRON_API kron_status kron_autotune(kron_stream_t stream, int kind, int n, int64_
                                    int* instances_per_tile, int* pipeline_depth);
 
 /*
+ * Full kernel configuration of a fixed-size (kind, n, io, comp), the search
+ * space of the autotuner.  The paper fixes one launch shape (5000 thread
+ * blocks, Sec. 5); here the body, the tile, the copy pipeline and the register
+ * blocking are chosen per configuration and per GPU.
+ *
+ *   variant:            the kernel body for contiguous batches (kron_variant);
+ *                       KRON_VARIANT_AUTO = the built-in choice
+ *   instances_per_tile: instances per CTA tile (0 = the body's default; the in-
+ *                       place bodies take the tile shapes listed above)
+ *   pipeline_depth:     tiles in flight per CTA (0 = default, 1..8)
+ *   fibers_per_step:    register blocking of the last contraction of the
+ *                       packed-pair bodies: 1 or 2 fibers per thread and step
+ *                       (0 = default)
+ *
+ * kron_set_kernel_config returns KRON_ERR_NOT_SUPPORTED when the body does not
+ * exist for (kind, n, io, comp) (in place: 2-D n = 16 any storage, FP32 2-D n =
+ * 10, 14, FP32 3-D n = 10, 14, 16, FP32 odd n; exchange: even n, FP32 or 16-bit
+ * storage; scalar: every real storage type) and KRON_ERR_INVALID_VALUE for
+ * values out of range; all-zero restores the built-in default.  Strided,
+ * transposed or misaligned batches always run the scalar body.  The split
+ * tensor path (KRON_COMPUTE_32F_BF16X3) and complex storage have one body each:
+ * only instances_per_tile and pipeline_depth apply there.
+ *
+ * kron_autotune_config times every configuration of that space on the
+ * caller's buffers (as kron_autotune; Y is overwritten), keeps the fastest
+ * unless the built-in default is within 2%, stores it in the process-wide
+ * table and in the tuning cache (KRON_TUNE_CACHE; entries are keyed by GPU
+ * name, SM count and driver version, so a cache written on another GPU or
+ * driver is ignored) and returns it.  kron_autotune is this search reduced to
+ * its instances-per-tile and pipeline-depth result.
+ */
+typedef enum {
+    KRON_VARIANT_AUTO = 0,
+    KRON_VARIANT_IN_PLACE = 1,   /* every contraction in place in the operand tile */
+    KRON_VARIANT_EXCHANGE = 2,   /* packed pairs, intermediates in separate exchange buffers */
+    KRON_VARIANT_SCALAR = 3      /* one fiber per thread, scalar FMA, exchange buffers */
+} kron_variant;
+
+typedef struct {
+    int variant;
+    int instances_per_tile;
+    int pipeline_depth;
+    int fibers_per_step;
+} kron_kernel_config;
+
+KRON_API kron_status kron_set_kernel_config(int kind, int n, kron_dtype io, kron_compute comp,
+                                            const kron_kernel_config* config);
+KRON_API kron_status kron_get_kernel_config(int kind, int n, kron_dtype io, kron_compute comp,
+                                            kron_kernel_config* config);
+KRON_API kron_status kron_autotune_config(kron_stream_t stream, int kind, int n, int64_t batch_count,
+                                          const void* X, void* Y, kron_dtype io, kron_compute comp,
+                                          kron_kernel_config* config);
+
+/*
  * Mixed-size batches (one launch for instances of different sizes and kinds).
  *
  * A class is one (kind, n) pair with its own shared components (square n x n,

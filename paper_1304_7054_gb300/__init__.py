@@ -46,6 +46,9 @@ SIGNATURES = {
     "kron_set_tile_config": ([_I, _I, _I, _I, _I, _I], _I),
     "kron_get_tile_config": ([_I, _I, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
     "kron_autotune": ([_P, _I, _I, _L, _P, _P, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
+    "kron_set_kernel_config": ([_I, _I, _I, _I, _P], _I),
+    "kron_get_kernel_config": ([_I, _I, _I, _I, _P], _I),
+    "kron_autotune_config": ([_P, _I, _I, _L, _P, _P, _I, _I, _P], _I),
     "kron_varlen_plan_create": ([ctypes.POINTER(_P), _I, _P, _L, _P, _P, _P, _I, _I], _I),
     "kron_varlen_workspace_size": ([_P, ctypes.POINTER(_S)], _I),
     "kron_varlen_execute": ([_P, _P, _P, _P, _S, _P], _I),
@@ -309,6 +312,46 @@ def autotune(kind, n, batch, X, Y, compute="native", stream=None):
                                         _io_of(X), COMPUTE[compute], ctypes.byref(p), ctypes.byref(d)),
            "kron_autotune")
     return p.value, d.value
+
+
+VARIANTS = {"auto": 0, "in_place": 1, "exchange": 2, "scalar": 3}
+
+
+class KernelConfig(ctypes.Structure):
+    """kron_kernel_config: kernel body, instances per tile, pipeline depth and
+    fibers per step of one fixed-size (kind, n, storage, compute)."""
+    _fields_ = [("variant", ctypes.c_int), ("instances_per_tile", ctypes.c_int), ("pipeline_depth", ctypes.c_int),
+                ("fibers_per_step", ctypes.c_int)]
+
+    def as_dict(self):
+        names = {v: k for k, v in VARIANTS.items()}
+        return {"variant": names.get(self.variant, self.variant), "instances_per_tile": self.instances_per_tile,
+                "pipeline_depth": self.pipeline_depth, "fibers_per_step": self.fibers_per_step}
+
+
+def set_kernel_config(kind, n, io, compute="native", variant="auto", instances_per_tile=0, pipeline_depth=0,
+                      fibers_per_step=0):
+    c = KernelConfig(VARIANTS[variant], instances_per_tile, pipeline_depth, fibers_per_step)
+    _check(load_library().kron_set_kernel_config(kind, n, DTYPES[io], COMPUTE[compute], ctypes.byref(c)),
+           "kron_set_kernel_config")
+
+
+def get_kernel_config(kind, n, io, compute="native") -> dict:
+    c = KernelConfig()
+    _check(load_library().kron_get_kernel_config(kind, n, DTYPES[io], COMPUTE[compute], ctypes.byref(c)),
+           "kron_get_kernel_config")
+    return c.as_dict()
+
+
+def autotune_config(kind, n, batch, X, Y, compute="native", stream=None) -> dict:
+    """Search kernel bodies, tiles, pipeline depths and fibers per step on X -> Y;
+    keeps the fastest (Y is overwritten) and returns it."""
+    c = KernelConfig()
+    need = batch * n ** kind
+    xp, yp = _device_operand(X, need, "X"), _device_operand(Y, need, "Y")
+    _check(load_library().kron_autotune_config(_stream_handle(stream), kind, n, batch, xp, yp, _io_of(X),
+                                               COMPUTE[compute], ctypes.byref(c)), "kron_autotune_config")
+    return c.as_dict()
 
 
 class _ClassDesc(ctypes.Structure):

@@ -217,7 +217,24 @@ static kron_status dispatch(KronDesc& d, cudaStream_t st) {
     if (d.io == KRON_C32F) return d.D == 2 ? launch_fiber_c32_d2(d, st) : launch_fiber_c32_d3(d, st);
     if (d.io == KRON_C64F) return d.D == 2 ? launch_fiber_c64_d2(d, st) : launch_fiber_c64_d3(d, st);
     if (d.comp == KRON_COMPUTE_32F_BF16X3) return launch_tc(d, st);
-    if (d.contiguous && d.ycontig && d.N % 2 == 0 && d.io != KRON_R64F) {
+    // An explicit kernel body (kron_set_kernel_config) for contiguous batches.
+    if (d.contiguous && d.ycontig && d.variant != KRON_VARIANT_AUTO) {
+        kron_status r = KRON_ERR_NOT_SUPPORTED;
+        if (d.variant == KRON_VARIANT_IN_PLACE) {
+            if (d.D == 2 && d.N == 16) r = launch_pair16(d, st);
+            else if (d.io == KRON_R32F && d.D == 2 && (d.N == 10 || d.N == 14)) r = launch_pair2ip(d, st);
+            else if (d.io == KRON_R32F && d.D == 3 && (d.N == 10 || d.N == 14 || d.N == 16)) r = launch_pair3ip(d, st);
+            else if (d.io == KRON_R32F && (d.N & 1) && d.N >= 3) r = launch_fiberip(d, st);
+        } else if (d.variant == KRON_VARIANT_EXCHANGE && d.N % 2 == 0) {
+            switch (d.io) {
+                case KRON_R32F: r = d.D == 2 ? launch_pair_f32_d2(d, st) : launch_pair_f32_d3(d, st); break;
+                case KRON_R16BF: r = d.D == 2 ? launch_pair_bf16_d2(d, st) : launch_pair_bf16_d3(d, st); break;
+                case KRON_R16F: r = d.D == 2 ? launch_pair_f16_d2(d, st) : launch_pair_f16_d3(d, st); break;
+                default: break;
+            }
+        }
+        if (r != KRON_ERR_NOT_SUPPORTED) return r;   // otherwise the scalar body below
+    } else if (d.contiguous && d.ycontig && d.N % 2 == 0 && d.io != KRON_R64F) {
         kron_status r = KRON_ERR_NOT_SUPPORTED;
         // In-place kernels where they beat the generic one (n = 16 in 2-D for every storage type).
         if (d.D == 2 && d.N == 16 && d.comp == KRON_COMPUTE_NATIVE) r = launch_pair16(d, st);
@@ -234,7 +251,7 @@ static kron_status dispatch(KronDesc& d, cudaStream_t st) {
         }
         if (r != KRON_ERR_NOT_SUPPORTED) return r;
     }
-    if ((d.N & 1) && d.N >= 3 && d.io == KRON_R32F && d.contiguous && d.ycontig) {
+    if ((d.N & 1) && d.N >= 3 && d.io == KRON_R32F && d.contiguous && d.ycontig && d.variant == KRON_VARIANT_AUTO) {
         const kron_status r = launch_fiberip(d, st);   // odd n, all contractions in place
         if (r != KRON_ERR_NOT_SUPPORTED) return r;
     }

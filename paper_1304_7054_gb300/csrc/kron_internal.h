@@ -45,6 +45,8 @@ struct KronDesc {
     int P = 0;           // instances per tile
     int nstage = -1;     // bulk-copy pipeline depth; 0 = generic loads; -1 = auto
     int grid = 0;        // CTAs; 0 = persistent (all resident CTAs)
+    int variant = 0;     // kernel body (kron_variant); 0 = built-in choice
+    int fps = 0;         // fibers per step of the last contraction; 0 = default
 };
 
 size_t elem_size(kron_dtype t);

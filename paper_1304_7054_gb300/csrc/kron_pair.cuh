@@ -243,7 +243,9 @@ __device__ __forceinline__ void last_stage(const PairArgs<N, D>& a, int F, Fetch
     }
 }
 
-template <typename S, int N, int D, int NT>
+// FPS: fibers per step of the last contraction (1, or 2 for more instruction-level
+// parallelism at the cost of registers).
+template <typename S, int N, int D, int NT, int FPS>
 __global__ void __launch_bounds__(NT) pair_kernel(const __grid_constant__ PairArgs<N, D> a) {
     using L = PairLayout<N, D, (int)sizeof(S)>;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -341,13 +343,21 @@ __global__ void __launch_bounds__(NT) pair_kernel(const __grid_constant__ PairAr
             const f2* m1p = reinterpret_cast<const f2*>(a.m1);
             const float* wb = ex1 + (it & 1) * (size_t)P * L::SQ;
             const int F = cnt * N;
-            for (int f = tid; f < F; f += NT) {
-                const int q = f / N, j = f - q * N;
-                float w[N];
-                load_row<N>(wb + q * L::SQ + L::SJ * j, w);
-                f2 y[N / 2];
-                contract_rows<N>(m1p, w, y);
-                pair_store<S, N, D>(a, Y + (inst0 + q) * L::NX + N * j, y);
+            if constexpr (FPS == 2) {
+                last_stage<S, N, D, NT>(a, F, [&](int f, float (&w)[N]) {
+                    const int q = f / N, j = f - q * N;
+                    load_row<N>(wb + q * L::SQ + L::SJ * j, w);
+                    return Y + (inst0 + q) * L::NX + N * j;
+                });
+            } else {
+                for (int f = tid; f < F; f += NT) {
+                    const int q = f / N, j = f - q * N;
+                    float w[N];
+                    load_row<N>(wb + q * L::SQ + L::SJ * j, w);
+                    f2 y[N / 2];
+                    contract_rows<N>(m1p, w, y);
+                    pair_store<S, N, D>(a, Y + (inst0 + q) * L::NX + N * j, y);
+                }
             }
             // W alternates between two buffers: the next tile's first stage writes the
             // other one, and the barrier after it orders this tile's reads before reuse.
@@ -376,14 +386,14 @@ __global__ void __launch_bounds__(NT) pair_kernel(const __grid_constant__ PairAr
                 }
             }
             const int F3 = cnt * N * N;
-            if constexpr (N >= 14) {   // two fibers per step: more ILP (measured faster at n = 16)
+            if constexpr (FPS == 2) {   // two fibers per step: more ILP
                 last_stage<S, N, D, NT>(a, F3, [&](int f, float (&u)[N]) {
                     const int q = f / (N * N), r = f - q * (N * N);
                     const int j = r % N, k = r / N;
                     load_row<N>(ex2 + q * L::SQ + L::SJ * j + L::SK * k, u);
                     return Y + (inst0 + q) * L::NX + N * j + N * N * k;
                 });
-            } else {                   // one fiber per step: fewer registers (faster at n = 10)
+            } else {                    // one fiber per step: fewer registers
                 const f2* m1p = reinterpret_cast<const f2*>(a.m1);
                 for (int f = tid; f < F3; f += NT) {
                     const int q = f / (N * N), r = f - q * (N * N);
@@ -406,10 +416,13 @@ size_t pair_smem_bytes(int P, int nstage) {
     return 128 + nstage * round_up((size_t)P * L::SX * sizeof(S), 128) + (size_t)P * (L::EX1 + L::EX2) * sizeof(float);
 }
 
-// Default tile: threads per CTA and instances per tile for each (N, kind).
+// Default tile: threads per CTA and instances per tile for each (N, kind), and
+// fibers per step of the last contraction (two measured faster for 3-D n >= 14,
+// one elsewhere).
 template <int N, int D>
 struct PairConfig {
     static constexpr int NT = 128;
+    static constexpr int FPS = (D == 3 && N >= 14) ? 2 : 1;
     // about one unit of first-stage work per thread
     static constexpr int P0 = (D == 2) ? (2 * NT) / N : ((2 * NT) / (N * N) > 0 ? (2 * NT) / (N * N) : 1);
 };
@@ -458,7 +471,8 @@ kron_status launch_pair_n(const KronDesc& d, cudaStream_t st) {
     if (smem > dev.smem_per_block_optin) return KRON_ERR_NOT_SUPPORTED;
     a.P = P;
     a.nstage = nstage;
-    auto kern = pair_kernel<S, N, D, NT>;
+    const int fps = d.fps > 0 ? d.fps : PairConfig<N, D>::FPS;
+    auto kern = fps == 2 ? pair_kernel<S, N, D, NT, 2> : pair_kernel<S, N, D, NT, 1>;
     if (!ensure_smem_optin((const void*)kern, smem)) return KRON_ERR_CUDA;
     const int64_t ntiles = (d.batch + P - 1) / P;
     int64_t grid = d.grid;

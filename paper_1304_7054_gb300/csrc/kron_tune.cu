@@ -1,12 +1,13 @@
-// Tile-configuration table and autotuner for the fixed-size kernels.
+// Kernel-configuration table and autotuner for the fixed-size kernels.
 //
-// A configuration is (instances per tile, bulk-copy pipeline depth) for one
-// (kind, n, storage type, compute mode).  kron_autotune times the candidates on
-// the caller's buffers with CUDA events and keeps the fastest; the table can be
-// persisted in a small text file named by the KRON_TUNE_CACHE environment
-// variable (one line per entry: device-name kind n io comp P depth; a later line
-// overrides an earlier one and "0 0" means the built-in default), read at first
-// use.
+// A configuration is (kernel body, instances per tile, bulk-copy pipeline depth,
+// fibers per step of the last contraction) for one (kind, n, storage type,
+// compute mode).  kron_autotune_config times the candidates on the caller's
+// buffers with CUDA events and keeps the fastest; the table can be persisted in
+// a small text file named by the KRON_TUNE_CACHE environment variable (one line
+// per entry: device-key kind n io comp P depth variant fps, the key being GPU
+// name, SM count and driver version; a later line overrides an earlier one and
+// all zeros mean the built-in default), read at first use.
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -25,20 +26,23 @@ namespace kron {
 namespace {
 
 using Key = std::tuple<int, int, int, int>;   // kind, n, io, comp
-struct Entry { int P, nstage; };
+struct Entry { int P, nstage, variant, fps; };
 
 std::mutex g_mu;
 std::map<Key, Entry> g_table;
 bool g_loaded = false;
 
-std::string device_name() {
-    int dev = 0;
+// Cache key of this GPU: name, SM count and driver version (a tuning result
+// holds for one chip configuration and one driver).
+std::string device_key() {
+    int dev = 0, drv = 0;
     cudaDeviceProp prop;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return "unknown";
+    cudaDriverGetVersion(&drv);
     std::string s = prop.name;
     for (char& c : s)
         if (c == ' ') c = '_';
-    return s;
+    return s + ":" + std::to_string(prop.multiProcessorCount) + ":" + std::to_string(drv);
 }
 
 void load_cache_locked() {
@@ -48,16 +52,17 @@ void load_cache_locked() {
     if (!path || !*path) return;
     FILE* f = fopen(path, "r");
     if (!f) return;
-    const std::string me = device_name();
-    char name[256];
-    int kind, n, io, comp, P, ns;
-    while (fscanf(f, "%255s %d %d %d %d %d %d", name, &kind, &n, &io, &comp, &P, &ns) == 7)
-        if (me == name) {
-            if (P == 0 && ns == 0)
-                g_table.erase(Key(kind, n, io, comp));   // a later tuning kept the default
-            else
-                g_table[Key(kind, n, io, comp)] = Entry{P, ns};
-        }
+    const std::string me = device_key();
+    char line[512], name[256];
+    while (fgets(line, sizeof(line), f)) {
+        int kind, n, io, comp, P, ns, var = 0, fps = 0;
+        const int got = sscanf(line, "%255s %d %d %d %d %d %d %d %d", name, &kind, &n, &io, &comp, &P, &ns, &var, &fps);
+        if (got < 7 || me != name) continue;
+        if (P == 0 && ns == 0 && var == 0 && fps == 0)
+            g_table.erase(Key(kind, n, io, comp));   // a later tuning kept the default
+        else
+            g_table[Key(kind, n, io, comp)] = Entry{P, ns, var, fps};
+    }
     fclose(f);
 }
 
@@ -66,9 +71,31 @@ void append_cache(const Key& k, const Entry& e) {
     if (!path || !*path) return;
     FILE* f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "%s %d %d %d %d %d %d\n", device_name().c_str(), std::get<0>(k), std::get<1>(k), std::get<2>(k),
-            std::get<3>(k), e.P, e.nstage);
+    fprintf(f, "%s %d %d %d %d %d %d %d %d\n", device_key().c_str(), std::get<0>(k), std::get<1>(k), std::get<2>(k),
+            std::get<3>(k), e.P, e.nstage, e.variant, e.fps);
     fclose(f);
+}
+
+bool real_io(kron_dtype io) { return io == KRON_R32F || io == KRON_R64F || io == KRON_R16BF || io == KRON_R16F; }
+
+// Whether kernel body `variant` exists for (kind, n, io, comp) and takes tile size P.
+bool variant_ok(int kind, int n, kron_dtype io, kron_compute comp, int variant, int P) {
+    if (variant == KRON_VARIANT_AUTO) return true;
+    if (comp != KRON_COMPUTE_NATIVE || !real_io(io)) return false;
+    const bool f32 = io == KRON_R32F, half = io == KRON_R16BF || io == KRON_R16F;
+    switch (variant) {
+        case KRON_VARIANT_IN_PLACE:
+            if (kind == 2 && n == 16 && (f32 || half)) return P == 0 || P == 16;
+            if (!f32) return false;
+            if (kind == 2 && (n == 10 || n == 14)) return P % 8 == 0;
+            if (kind == 3 && n == 16) return P <= 1;
+            if (kind == 3 && (n == 10 || n == 14)) return P == 0 || P == 4;
+            if ((n & 1) && n >= 3) return P % 4 == 0;
+            return false;
+        case KRON_VARIANT_EXCHANGE: return (n % 2 == 0) && (f32 || half);
+        case KRON_VARIANT_SCALAR: return true;
+        default: return false;
+    }
 }
 
 }  // namespace
@@ -80,12 +107,14 @@ void apply_tile_config(KronDesc& d) {
     if (it != g_table.end()) {
         if (d.P <= 0) d.P = it->second.P;
         if (d.nstage < 0) d.nstage = it->second.nstage > 0 ? it->second.nstage : -1;
+        d.variant = it->second.variant;
+        d.fps = it->second.fps;
     }
 }
 
 void tune_cache_append(int kind, int n, kron_dtype io, kron_compute comp, int P, int nstage) {
     std::lock_guard<std::mutex> lock(g_mu);
-    append_cache(Key(kind, n, (int)io, (int)comp), Entry{P, nstage});
+    append_cache(Key(kind, n, (int)io, (int)comp), Entry{P, nstage, 0, 0});
 }
 
 }  // namespace kron
@@ -93,6 +122,36 @@ void tune_cache_append(int kind, int n, kron_dtype io, kron_compute comp, int P,
 using namespace kron;
 
 extern "C" {
+
+KRON_API kron_status kron_set_kernel_config(int kind, int n, kron_dtype io, kron_compute comp,
+                                            const kron_kernel_config* c) {
+    if (!c || (kind != 2 && kind != 3) || n < 1 || n > kMaxN || c->instances_per_tile < 0 ||
+        c->instances_per_tile > 4096 || c->pipeline_depth < 0 || c->pipeline_depth > 8 || c->fibers_per_step < 0 ||
+        c->fibers_per_step > 2 || c->variant < 0 || c->variant > KRON_VARIANT_SCALAR)
+        return KRON_ERR_INVALID_VALUE;
+    if (!variant_ok(kind, n, io, comp, c->variant, c->instances_per_tile)) return KRON_ERR_NOT_SUPPORTED;
+    std::lock_guard<std::mutex> lock(g_mu);
+    load_cache_locked();
+    if (c->instances_per_tile == 0 && c->pipeline_depth == 0 && c->variant == 0 && c->fibers_per_step == 0)
+        g_table.erase(Key(kind, n, (int)io, (int)comp));
+    else
+        g_table[Key(kind, n, (int)io, (int)comp)] =
+            Entry{c->instances_per_tile, c->pipeline_depth, c->variant, c->fibers_per_step};
+    return KRON_OK;
+}
+
+KRON_API kron_status kron_get_kernel_config(int kind, int n, kron_dtype io, kron_compute comp, kron_kernel_config* c) {
+    if (!c) return KRON_ERR_INVALID_VALUE;
+    std::lock_guard<std::mutex> lock(g_mu);
+    load_cache_locked();
+    auto it = g_table.find(Key(kind, n, (int)io, (int)comp));
+    const Entry e = it == g_table.end() ? Entry{0, 0, 0, 0} : it->second;
+    c->variant = e.variant;
+    c->instances_per_tile = e.P;
+    c->pipeline_depth = e.nstage;
+    c->fibers_per_step = e.fps;
+    return KRON_OK;
+}
 
 KRON_API kron_status kron_set_tile_config(int kind, int n, kron_dtype io, kron_compute comp, int instances_per_tile,
                                           int pipeline_depth) {
@@ -104,24 +163,22 @@ KRON_API kron_status kron_set_tile_config(int kind, int n, kron_dtype io, kron_c
     if (instances_per_tile == 0 && pipeline_depth == 0)
         g_table.erase(Key(kind, n, (int)io, (int)comp));
     else
-        g_table[Key(kind, n, (int)io, (int)comp)] = Entry{instances_per_tile, pipeline_depth};
+        g_table[Key(kind, n, (int)io, (int)comp)] = Entry{instances_per_tile, pipeline_depth, 0, 0};
     return KRON_OK;
 }
 
 KRON_API kron_status kron_get_tile_config(int kind, int n, kron_dtype io, kron_compute comp,
                                           int* instances_per_tile, int* pipeline_depth) {
     if (!instances_per_tile || !pipeline_depth) return KRON_ERR_INVALID_VALUE;
-    std::lock_guard<std::mutex> lock(g_mu);
-    load_cache_locked();
-    auto it = g_table.find(Key(kind, n, (int)io, (int)comp));
-    *instances_per_tile = it == g_table.end() ? 0 : it->second.P;
-    *pipeline_depth = it == g_table.end() ? 0 : it->second.nstage;
+    kron_kernel_config c;
+    kron_get_kernel_config(kind, n, io, comp, &c);
+    *instances_per_tile = c.instances_per_tile;
+    *pipeline_depth = c.pipeline_depth;
     return KRON_OK;
 }
 
-KRON_API kron_status kron_autotune(kron_stream_t stream, int kind, int n, int64_t batch_count, const void* X,
-                                   void* Y, kron_dtype io, kron_compute comp, int* instances_per_tile,
-                                   int* pipeline_depth) {
+KRON_API kron_status kron_autotune_config(kron_stream_t stream, int kind, int n, int64_t batch_count, const void* X,
+                                          void* Y, kron_dtype io, kron_compute comp, kron_kernel_config* out) {
     if ((kind != 2 && kind != 3) || n < 1 || n > kMaxN || batch_count < 1 || !X || !Y) return KRON_ERR_INVALID_VALUE;
     cudaStream_t st = (cudaStream_t)stream;
     // Components do not change the timing; identity keeps the outputs finite.
@@ -144,32 +201,56 @@ KRON_API kron_status kron_autotune(kron_stream_t stream, int kind, int n, int64_
                              comp_ptr, n, X, n, n * n, (int64_t)n * n * n, be, Y, n, n * n, (int64_t)n * n * n, io,
                              comp);
     };
-    int def_P = 0, def_ns = 0;
-    kron_get_tile_config(kind, n, io, comp, &def_P, &def_ns);
-    // Candidates: the built-in default (0, 0) first, then tiles of half, one, two
-    // and four times "one fiber per thread" with pipeline depths 1 to 3.  Each is
-    // timed as the best of three rounds of 10 launches; a candidate replaces the
-    // default only if it is at least 2% faster (timing noise would otherwise pick
-    // configurations at random).
-    std::vector<Entry> cands;
-    cands.push_back(Entry{0, 0});
+    kron_kernel_config prev;
+    kron_get_kernel_config(kind, n, io, comp, &prev);
+    // Candidates: the built-in default first; then every body that exists for
+    // this configuration with tiles of half, one, two and four times "one
+    // fiber per thread" (the in-place bodies: their own tile shapes), pipeline
+    // depths 1 and 2, and for the packed-pair bodies one or two fibers per step.
+    std::vector<kron_kernel_config> cands;
+    cands.push_back(kron_kernel_config{0, 0, 0, 0});
     const int base = kind == 2 ? (256 + n - 1) / n : (256 + n * n - 1) / (n * n);
-    for (int mul2 : {1, 2, 4, 8})
-        for (int ns : {1, 2, 3}) cands.push_back(Entry{std::max(1, base * mul2 / 2), ns});
+    for (int var = KRON_VARIANT_IN_PLACE; var <= KRON_VARIANT_SCALAR; ++var) {
+        if (!variant_ok(kind, n, io, comp, var, 0) && var != KRON_VARIANT_IN_PLACE) continue;
+        std::vector<int> tiles;
+        if (var == KRON_VARIANT_IN_PLACE) {
+            for (int P : {0, 4, 8, 12, 16, 24, 32})
+                if (variant_ok(kind, n, io, comp, var, P) && (P == 0 || (n & 1) || (kind == 2 && n != 16)))
+                    tiles.push_back(P);
+        } else {
+            for (int mul2 : {1, 2, 4, 8}) tiles.push_back(std::max(1, base * mul2 / 2));
+        }
+        for (int P : tiles)
+            for (int ns : {1, 2})
+                for (int fps : {1, 2}) {
+                    if (fps == 2 && var != KRON_VARIANT_EXCHANGE) continue;
+                    cands.push_back(kron_kernel_config{var, P, ns, var == KRON_VARIANT_EXCHANGE ? fps : 0});
+                }
+    }
+    if (comp != KRON_COMPUTE_NATIVE || !real_io(io)) {   // one body: tile and depth only
+        cands.resize(1);
+        for (int mul2 : {1, 2, 4, 8})
+            for (int ns : {1, 2}) cands.push_back(kron_kernel_config{0, std::max(1, base * mul2 / 2), ns, 0});
+    }
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return KRON_ERR_CUDA;
     float best = 1e30f, t_default = 1e30f;
-    Entry best_e{0, 0};
+    kron_kernel_config best_c{0, 0, 0, 0};
     kron_status rs = KRON_OK;
-    for (const Entry& c : cands) {
-        kron_set_tile_config(kind, n, io, comp, c.P, c.nstage);
-        bool ok = true;
-        for (int w = 0; w < 2 && ok; ++w) ok = run() == KRON_OK;
-        if (!ok) continue;
+    for (const kron_kernel_config& c : cands) {
+        {
+            std::lock_guard<std::mutex> lock(g_mu);
+            if (c.variant == 0 && c.instances_per_tile == 0 && c.pipeline_depth == 0 && c.fibers_per_step == 0)
+                g_table.erase(Key(kind, n, (int)io, (int)comp));
+            else
+                g_table[Key(kind, n, (int)io, (int)comp)] =
+                    Entry{c.instances_per_tile, c.pipeline_depth, c.variant, c.fibers_per_step};
+        }
+        if (run() != KRON_OK) continue;   // not available at this size (e.g. shared memory)
         float t = 1e30f;
-        for (int round = 0; round < 3; ++round) {
+        for (int round = 0; round < 2; ++round) {
             cudaEventRecord(e0, st);
-            for (int r = 0; r < 10; ++r) run();
+            for (int r = 0; r < 5; ++r) run();
             cudaEventRecord(e1, st);
             if (cudaEventSynchronize(e1) != cudaSuccess) { rs = KRON_ERR_CUDA; break; }
             float ms = 0;
@@ -177,23 +258,36 @@ KRON_API kron_status kron_autotune(kron_stream_t stream, int kind, int n, int64_
             t = std::min(t, ms);
         }
         if (rs != KRON_OK) break;
-        if (c.P == 0 && c.nstage == 0) t_default = t;
-        if (t < best) { best = t; best_e = c; }
+        if (c.variant == 0 && c.instances_per_tile == 0 && c.pipeline_depth == 0) t_default = t;
+        if (t < best) { best = t; best_c = c; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rs != KRON_OK) {
-        kron_set_tile_config(kind, n, io, comp, def_P, def_ns);
+        kron_set_kernel_config(kind, n, io, comp, &prev);
         return rs;
     }
-    if (best > 0.98f * t_default) best_e = Entry{0, 0};   // not clearly better: keep the default
-    kron_set_tile_config(kind, n, io, comp, best_e.P, best_e.nstage);
+    if (best > 0.98f * t_default) best_c = kron_kernel_config{0, 0, 0, 0};   // not clearly better: keep the default
     {
         std::lock_guard<std::mutex> lock(g_mu);
-        append_cache(Key(kind, n, (int)io, (int)comp), best_e);   // "0 0" records "default kept"
+        const Entry e{best_c.instances_per_tile, best_c.pipeline_depth, best_c.variant, best_c.fibers_per_step};
+        if (e.P == 0 && e.nstage == 0 && e.variant == 0 && e.fps == 0)
+            g_table.erase(Key(kind, n, (int)io, (int)comp));
+        else
+            g_table[Key(kind, n, (int)io, (int)comp)] = e;
+        append_cache(Key(kind, n, (int)io, (int)comp), e);   // all zero records "default kept"
     }
-    if (instances_per_tile) *instances_per_tile = best_e.P;
-    if (pipeline_depth) *pipeline_depth = best_e.nstage;
+    if (out) *out = best_c;
+    return KRON_OK;
+}
+
+KRON_API kron_status kron_autotune(kron_stream_t stream, int kind, int n, int64_t batch_count, const void* X, void* Y,
+                                   kron_dtype io, kron_compute comp, int* instances_per_tile, int* pipeline_depth) {
+    kron_kernel_config c;
+    const kron_status r = kron_autotune_config(stream, kind, n, batch_count, X, Y, io, comp, &c);
+    if (r != KRON_OK) return r;
+    if (instances_per_tile) *instances_per_tile = c.instances_per_tile;
+    if (pipeline_depth) *pipeline_depth = c.pipeline_depth;
     return KRON_OK;
 }
 

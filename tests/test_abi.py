@@ -179,3 +179,34 @@ def test_peak_probe_rejects_bad_arguments(lib):
     assert lib.kron_peak_probe(None, 3, 10, ctypes.byref(f)) == INVALID
     assert lib.kron_peak_probe(None, 0, 0, ctypes.byref(f)) == INVALID
     assert lib.kron_peak_probe(None, 0, 10, None) == INVALID
+
+
+NOTSUP_ = 2
+
+
+def test_kernel_config_validation_and_round_trip(lib):
+    cfg = kg.KernelConfig
+    f32 = kg.DTYPES["f32"]
+    # out of range
+    assert lib.kron_set_kernel_config(2, 16, f32, 0, ctypes.byref(cfg(9, 0, 0, 0))) == INVALID
+    assert lib.kron_set_kernel_config(2, 16, f32, 0, ctypes.byref(cfg(2, 0, 9, 0))) == INVALID
+    assert lib.kron_set_kernel_config(2, 16, f32, 0, ctypes.byref(cfg(2, 0, 0, 3))) == INVALID
+    assert lib.kron_set_kernel_config(2, 17, f32, 0, ctypes.byref(cfg(0, 0, 0, 0))) == INVALID
+    assert lib.kron_set_kernel_config(2, 16, f32, 0, None) == INVALID
+    # bodies that do not exist for the configuration
+    assert lib.kron_set_kernel_config(2, 12, f32, 0, ctypes.byref(cfg(1, 0, 0, 0))) == NOTSUP_   # no in-place 2-D n=12
+    assert lib.kron_set_kernel_config(2, 7, f32, 0, ctypes.byref(cfg(2, 0, 0, 0))) == NOTSUP_    # pairs need even n
+    assert lib.kron_set_kernel_config(2, 16, kg.DTYPES["f64"], 0, ctypes.byref(cfg(2, 0, 0, 0))) == NOTSUP_
+    assert lib.kron_set_kernel_config(2, 16, f32, 1, ctypes.byref(cfg(3, 0, 0, 0))) == NOTSUP_   # tensor path: one body
+    assert lib.kron_set_kernel_config(2, 16, f32, 0, ctypes.byref(cfg(1, 7, 0, 0))) == NOTSUP_   # in place takes 16
+    # round trip, then back to the default
+    assert lib.kron_set_kernel_config(3, 12, f32, 0, ctypes.byref(cfg(2, 6, 2, 2))) == 0
+    got = cfg()
+    assert lib.kron_get_kernel_config(3, 12, f32, 0, ctypes.byref(got)) == 0
+    assert (got.variant, got.instances_per_tile, got.pipeline_depth, got.fibers_per_step) == (2, 6, 2, 2)
+    p, d = ctypes.c_int(), ctypes.c_int()
+    assert lib.kron_get_tile_config(3, 12, f32, 0, ctypes.byref(p), ctypes.byref(d)) == 0
+    assert (p.value, d.value) == (6, 2)
+    assert lib.kron_set_kernel_config(3, 12, f32, 0, ctypes.byref(cfg(0, 0, 0, 0))) == 0
+    assert lib.kron_get_kernel_config(3, 12, f32, 0, ctypes.byref(got)) == 0
+    assert (got.variant, got.instances_per_tile, got.pipeline_depth, got.fibers_per_step) == (0, 0, 0, 0)

@@ -7,8 +7,15 @@ import pytest
 import paper_1304_7054_gb300 as kg
 from paper_1304_7054_gb300 import inputs
 
-from helpers import TOL, max_norm_err, oracle_ref
+from helpers import TOL, max_norm_err, oracle_ref, storage_check
 from test_gpu_fiber import run_gpu
+
+
+def check(Y, b, X64, io):
+    if io in ("bf16", "f16"):
+        assert storage_check(Y, b, X64, io) <= 1.0
+    else:
+        assert max_norm_err(Y, oracle_ref(b, X64), b, X64) <= TOL[io]
 
 pytestmark = pytest.mark.gpu
 
@@ -24,7 +31,7 @@ def test_tile_configs_give_the_same_result(kind, n, io, P, depth):
         Y, X64 = run_gpu(b, io=io, guard=8)
     finally:
         kg.set_tile_config(kind, n, io, "native", 0, 0)
-    assert max_norm_err(Y, oracle_ref(b, X64), b, X64, io) <= TOL[io]
+    check(Y, b, X64, io)
 
 
 @pytest.mark.parametrize("kind,n", [(2, 16), (3, 16), (2, 9)])
@@ -34,11 +41,55 @@ def test_autotune_then_correct(kind, n):
     X = torch.from_numpy(b.X).cuda()
     scratch = torch.empty_like(X)
     P, depth = kg.autotune(kind, n, b.batch, X, scratch)
-    # (0, 0) means no candidate beat the built-in default clearly enough.
-    assert (P, depth) == (0, 0) or (P >= 1 and depth >= 1)
+    # (0, 0) means no candidate beat the built-in default clearly enough; a tile
+    # of 0 with a depth is a body's own tile shape with another pipeline depth.
+    assert P >= 0 and 0 <= depth <= 8
     assert kg.get_tile_config(kind, n, "f32") == (P, depth)
     try:
         Y, X64 = run_gpu(b)
     finally:
-        kg.set_tile_config(kind, n, "f32", "native", 0, 0)
+        kg.set_kernel_config(kind, n, "f32")
     assert max_norm_err(Y, oracle_ref(b, X64), b, X64) <= TOL["f32"]
+
+
+# Every kernel body the tuner can choose, with tiles, pipeline depths and fibers
+# per step, computes the same operation (a body that does not exist for the
+# configuration is refused when it is set).
+CONFIGS = [("in_place", 0, 1, 0), ("in_place", 0, 2, 0), ("exchange", 0, 1, 1), ("exchange", 0, 2, 2),
+           ("exchange", 7, 1, 2), ("scalar", 0, 1, 0), ("scalar", 5, 2, 0)]
+
+
+@pytest.mark.parametrize("kind,n,io", [(2, 16, "f32"), (3, 16, "f32"), (2, 10, "f32"), (3, 10, "f32"), (2, 16, "bf16"),
+                                       (3, 12, "f16"), (2, 15, "f32"), (3, 7, "f32"), (2, 8, "f64")])
+@pytest.mark.parametrize("variant,P,depth,fps", CONFIGS)
+def test_kernel_configs_give_the_same_result(kind, n, io, variant, P, depth, fps):
+    b = inputs.make_batch(kind, n, 333 if kind == 2 else 45, seed=540 + n, x_dist="normal",
+                          dtype=np.float64 if io == "f64" else np.float32)
+    try:
+        kg.set_kernel_config(kind, n, io, "native", variant, P, depth, fps)
+    except kg.KronError as e:
+        assert e.status == 2   # KRON_ERR_NOT_SUPPORTED: no such body here
+        return
+    try:
+        assert kg.get_kernel_config(kind, n, io)["variant"] == variant
+        Y, X64 = run_gpu(b, io=io, guard=8)
+    finally:
+        kg.set_kernel_config(kind, n, io)
+    check(Y, b, X64, io)
+
+
+@pytest.mark.parametrize("kind,n,io", [(3, 16, "f32"), (2, 12, "bf16"), (3, 9, "f32")])
+def test_autotune_config_then_correct(kind, n, io):
+    import torch
+    from paper_1304_7054_gb300 import inputs as inp
+    b = inputs.make_batch(kind, n, 4096 if kind == 2 else 600, seed=560 + n, x_dist="normal")
+    xt = inp.to_storage(b.X, io) if io != "f32" else torch.from_numpy(b.X)
+    X = xt.cuda()
+    cfg = kg.autotune_config(kind, n, b.batch, X, torch.empty_like(X))
+    assert cfg == kg.get_kernel_config(kind, n, io)
+    assert cfg["variant"] in kg.VARIANTS
+    try:
+        Y, X64 = run_gpu(b, io=io)
+    finally:
+        kg.set_kernel_config(kind, n, io)
+    check(Y, b, X64, io)
