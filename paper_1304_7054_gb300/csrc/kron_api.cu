@@ -269,7 +269,8 @@ static kron_status check_modes(kron_dtype io, kron_compute comp) {
         return KRON_ERR_INVALID_VALUE;
     if (comp == KRON_COMPUTE_NATIVE) return KRON_OK;
     if (is_complex(io)) return comp == KRON_COMPUTE_32F_BF16X3 ? KRON_ERR_NOT_SUPPORTED : KRON_ERR_INVALID_VALUE;
-    if (comp == KRON_COMPUTE_32F_BF16X3) return (io == KRON_R32F || io == KRON_R16BF) ? KRON_OK : KRON_ERR_NOT_SUPPORTED;
+    if (comp == KRON_COMPUTE_32F_BF16X3)
+        return (io == KRON_R32F || io == KRON_R16BF || io == KRON_R16F) ? KRON_OK : KRON_ERR_NOT_SUPPORTED;
     return KRON_ERR_INVALID_VALUE;
 }
 

@@ -303,14 +303,18 @@ struct TcArgs3 {
     unsigned* err;
 };
 
-// n < 16: T has its own 16 KB buffer, so the operand buffer is free after modes
-// 1 and 2 and the next instance is fetched while mode 3 runs.  n = 16: T rows
-// overwrite the operand planes (a separate T buffer halves the resident warps and
-// measured 1.32x slower), so the next fetch waits for mode 3.
-template <int N>
+// n < 16 or 16-bit storage: T has its own 16 KB buffer, so the operand buffer is
+// free after modes 1 and 2 and the next instance is fetched while mode 3 runs.
+// n = 16 with FP32 storage: T rows overwrite the operand planes (a separate T
+// buffer halves the resident warps and measured 1.32x slower), so the next fetch
+// waits for mode 3.
+template <typename S, int N>
 struct Tc3Layout {
-    static constexpr uint32_t XB = (uint32_t)round_up((size_t)N * N * N * 4, 128);  // FP32 instance
-    static constexpr bool INPLACE = (N == 16);      // T rows overwrite the operand planes
+    // the instance, at its alignment phase when n^3 elements are not a whole
+    // number of 16-byte units (odd n): the copy takes the aligned span around it
+    static constexpr bool ALIGNED = (N * N * N * sizeof(S)) % 16 == 0;
+    static constexpr uint32_t XB = (uint32_t)round_up((size_t)N * N * N * sizeof(S) + (ALIGNED ? 0 : 32), 128);
+    static constexpr bool INPLACE = (N == 16 && sizeof(S) == 4);   // T rows overwrite the operand planes
     static constexpr uint32_t TB = INPLACE ? 0u : 16384u;
     static constexpr uint32_t PER_WARP = XB + TB;
 };
@@ -330,26 +334,30 @@ __device__ __forceinline__ uint32_t trow_off(int p, int c) {
     return (uint32_t)(p * 1024 + 16 * ((c ^ (p & 7) ^ ((c >> 3) & 1)) & 31));
 }
 
-template <int N>
-__device__ __forceinline__ float xval(const float* xs, int l, int m, int p) {
-    if constexpr (N == 16) return xs[l + 16 * m + 256 * p];
-    else return (l < N && m < N) ? xs[l + N * m + N * N * p] : 0.f;
+template <typename S, int N>
+__device__ __forceinline__ float xval(const S* xs, int l, int m, int p) {
+    if constexpr (N == 16) return load_cvt<float, S>(xs[l + 16 * m + 256 * p]);
+    else return (l < N && m < N) ? load_cvt<float, S>(xs[l + N * m + N * N * p]) : 0.f;
 }
 
 // Modes 1 and 2 of plane p: writes row p of T (hi and lo halves).
-template <int N>
-__device__ __forceinline__ void tc3_plane_load(const float* xs, int p, int g, int t, unsigned (&bh)[4],
+template <typename S, int N>
+__device__ __forceinline__ void tc3_plane_load(const S* xs, int p, int g, int t, unsigned (&bh)[4],
                                                unsigned (&bl)[4]) {
     // B fragment of X_p^T for n-tiles nt = 0, 1: column n = l = 8 nt + g,
     // rows k = m = 2t, 2t+1 and 2t+8, 2t+9
 #pragma unroll
     for (int nt = 0; nt < 2; ++nt) {
         const int l = 8 * nt + g;
-        split_pair(xval<N>(xs, l, 2 * t, p), xval<N>(xs, l, 2 * t + 1, p), bh[2 * nt], bl[2 * nt]);
-        split_pair(xval<N>(xs, l, 2 * t + 8, p), xval<N>(xs, l, 2 * t + 9, p), bh[2 * nt + 1], bl[2 * nt + 1]);
+        split_pair(xval<S, N>(xs, l, 2 * t, p), xval<S, N>(xs, l, 2 * t + 1, p), bh[2 * nt], bl[2 * nt]);
+        split_pair(xval<S, N>(xs, l, 2 * t + 8, p), xval<S, N>(xs, l, 2 * t + 9, p), bh[2 * nt + 1],
+                   bl[2 * nt + 1]);
     }
 }
 
+// XEXACT: the operand is a bfloat16 value (bf16 storage), so its lo part is zero
+// and the product with it is skipped.
+template <bool XEXACT>
 __device__ __forceinline__ void tc3_plane_compute(const unsigned (&bh)[4], const unsigned (&bl)[4],
                                                   const unsigned (&m2h)[4], const unsigned (&m2l)[4],
                                                   const unsigned (&m1h)[2][2], const unsigned (&m1l)[2][2],
@@ -360,7 +368,7 @@ __device__ __forceinline__ void tc3_plane_compute(const unsigned (&bh)[4], const
 #pragma unroll
         for (int e = 0; e < 4; ++e) w[nt][e] = 0.f;
         mma_bf16_16816(w[nt], m2l, bh[2 * nt], bh[2 * nt + 1]);
-        mma_bf16_16816(w[nt], m2h, bl[2 * nt], bl[2 * nt + 1]);
+        if constexpr (!XEXACT) mma_bf16_16816(w[nt], m2h, bl[2 * nt], bl[2 * nt + 1]);
         mma_bf16_16816(w[nt], m2h, bh[2 * nt], bh[2 * nt + 1]);
     }
     unsigned wh[4], wl[4];
@@ -394,8 +402,8 @@ __device__ __forceinline__ void tc3_plane_store(unsigned char* tb, int p, int g,
     }
 }
 
-template <int N>
-__device__ __forceinline__ void tc3_rows(const TcArgs3<N>& a, float* yq, uint32_t tb_s, int mt, int lane,
+template <typename S, int N>
+__device__ __forceinline__ void tc3_rows(const TcArgs3<N>& a, S* yq, uint32_t tb_s, int mt, int lane,
                                          const unsigned (&m3h)[2][2], const unsigned (&m3l)[2][2]) {
     const int g = lane >> 2, t = lane & 3, mi = lane >> 3, rr = lane & 7;
     unsigned ah[4], al[4];
@@ -412,25 +420,30 @@ __device__ __forceinline__ void tc3_rows(const TcArgs3<N>& a, float* yq, uint32_
         for (int e = 0; e < 4; ++e) {
             const int i = g + 8 * (e >> 1), k = 8 * nt + 2 * t + (e & 1);
             if (i < N && k < N) {
-                float* dst = yq + i + N * mt + N * N * k;
+                S* dst = yq + i + N * mt + N * N * k;
                 float v = a.alpha_one ? y[e] : a.alpha * y[e];
-                if (!a.beta_zero) v = fmaf(a.beta, *dst, v);
-                __stcs(dst, v);
+                if (!a.beta_zero) v = fmaf(a.beta, load_cvt<float, S>(*dst), v);
+                if constexpr (sizeof(S) == 4)
+                    __stcs(reinterpret_cast<float*>(dst), v);
+                else
+                    *dst = store_cvt<S, float>(v);
             }
         }
     }
 }
 
-template <int N>
+template <typename S, int N>
 __global__ void __launch_bounds__(32 * kTc3Warps) tc3_kernel(const __grid_constant__ TcArgs3<N> a) {
-    using L = Tc3Layout<N>;
+    using L = Tc3Layout<S, N>;
     constexpr int NX = N * N * N;
+    constexpr unsigned NXB = NX * (unsigned)sizeof(S);
+    constexpr bool XEXACT = std::is_same<S, __nv_bfloat16>::value;
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane >> 2, t = lane & 3;
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem) + warp;
     unsigned char* wb = smem + 128 + (size_t)warp * L::PER_WARP;
-    float* xs = reinterpret_cast<float*>(wb);               // FP32 instance (planes of N^2 values)
+    S* xs = reinterpret_cast<S*>(wb);                       // the instance (planes of N^2 values)
     unsigned char* tb = L::INPLACE ? wb : wb + L::XB;        // T rows, 1 KB each
     const uint32_t tb_s = smem_u32(tb);
 
@@ -458,30 +471,40 @@ __global__ void __launch_bounds__(32 * kTc3Warps) tc3_kernel(const __grid_consta
     const int64_t nwarps = (int64_t)gridDim.x * kTc3Warps;
     int64_t inst = (int64_t)blockIdx.x * kTc3Warps + warp;
     uint64_t pol = 0;
+    // Instance q: its 16-byte-aligned span is copied, the instance starts `phase(q)`
+    // elements into the buffer (0 whenever n^3 elements are whole 16-byte units).
+    auto phase = [&](int64_t q) -> int {
+        if constexpr (L::ALIGNED) return 0;
+        else return (int)(((uintptr_t)(static_cast<const S*>(a.X) + q * NX) & 15u) / sizeof(S));
+    };
+    auto fetch = [&](int64_t q) {
+        const int ph = phase(q);
+        const unsigned bytes = (unsigned)(ph * sizeof(S) + NXB + 15u) & ~15u;
+        mbar_arrive_expect_tx(bar, bytes);
+        bulk_g2s(xs, static_cast<const S*>(a.X) + q * NX - ph, bytes, bar, pol);
+    };
     if (lane == 0) {
         mbar_init(bar, 1);
         fence_barrier_init();
         pol = l2_evict_first_policy();
-        if (inst < a.batch) {
-            mbar_arrive_expect_tx(bar, NX * 4);
-            bulk_g2s(xs, static_cast<const float*>(a.X) + inst * NX, NX * 4, bar, pol);
-        }
+        if (inst < a.batch) fetch(inst);
     }
     __syncwarp();
-    unsigned phase = 0;
-    for (; inst < a.batch; inst += nwarps, phase ^= 1u) {
-        if (!mbar_wait_bounded(bar, phase, a.err)) return;   // nothing else in flight
+    unsigned bphase = 0;
+    for (; inst < a.batch; inst += nwarps, bphase ^= 1u) {
+        if (!mbar_wait_bounded(bar, bphase, a.err)) return;   // nothing else in flight
+        const S* xq = xs + phase(inst);
 
         // ---- modes 1 and 2, two planes per step ------------------------------------------
 #pragma unroll 1
         for (int p = 0; p < N; p += 2) {
             const bool two = p + 1 < N;
             unsigned bh0[4], bl0[4], bh1[4], bl1[4];
-            tc3_plane_load<N>(xs, p, g, t, bh0, bl0);
-            if (two) tc3_plane_load<N>(xs, p + 1, g, t, bh1, bl1);
+            tc3_plane_load<S, N>(xq, p, g, t, bh0, bl0);
+            if (two) tc3_plane_load<S, N>(xq, p + 1, g, t, bh1, bl1);
             float z0[2][4], z1[2][4];
-            tc3_plane_compute(bh0, bl0, m2h, m2l, m1h, m1l, z0);
-            if (two) tc3_plane_compute(bh1, bl1, m2h, m2l, m1h, m1l, z1);
+            tc3_plane_compute<XEXACT>(bh0, bl0, m2h, m2l, m1h, m1l, z0);
+            if (two) tc3_plane_compute<XEXACT>(bh1, bl1, m2h, m2l, m1h, m1l, z1);
             __syncwarp();   // planes p, p+1 are read by every lane before they are overwritten
             tc3_plane_store(tb, p, g, t, z0);
             if (two) tc3_plane_store(tb, p + 1, g, t, z1);
@@ -492,19 +515,18 @@ __global__ void __launch_bounds__(32 * kTc3Warps) tc3_kernel(const __grid_consta
                 const int64_t next = inst + nwarps;
                 if (next < a.batch) {
                     fence_proxy_async_smem();
-                    mbar_arrive_expect_tx(bar, NX * 4);
-                    bulk_g2s(xs, static_cast<const float*>(a.X) + next * NX, NX * 4, bar, pol);
+                    fetch(next);
                 }
             }
         };
         if constexpr (!L::INPLACE) fetch_next();   // the operand planes are no longer read
 
         // ---- mode 3, two row blocks per step ---------------------------------------------
-        float* yq = static_cast<float*>(a.Y) + inst * NX;
+        S* yq = static_cast<S*>(a.Y) + inst * NX;
 #pragma unroll 1
         for (int mt = 0; mt < N; mt += 2) {
-            tc3_rows<N>(a, yq, tb_s, mt, lane, m3h, m3l);
-            if (mt + 1 < N) tc3_rows<N>(a, yq, tb_s, mt + 1, lane, m3h, m3l);
+            tc3_rows<S, N>(a, yq, tb_s, mt, lane, m3h, m3l);
+            if (mt + 1 < N) tc3_rows<S, N>(a, yq, tb_s, mt + 1, lane, m3h, m3l);
         }
         __syncwarp();   // T is free (in place: so are the operand planes)
         if constexpr (L::INPLACE) fetch_next();
@@ -596,7 +618,7 @@ static kron_status launch_tc2_n(const KronDesc& d, cudaStream_t st) {
     return cudaPeekAtLastError() == cudaSuccess ? KRON_OK : KRON_ERR_CUDA;
 }
 
-template <int N>
+template <typename S, int N>
 static kron_status launch_tc3_n(const KronDesc& d, cudaStream_t st) {
     const DeviceInfo& dev = device_info();
     if (dev.sms <= 0) return KRON_ERR_CUDA;
@@ -613,9 +635,9 @@ static kron_status launch_tc3_n(const KronDesc& d, cudaStream_t st) {
     a.alpha_one = d.alpha == 1.0;
     a.err = device_error_word();
     if (!a.err) return KRON_ERR_CUDA;
-    const size_t smem = 128 + kTc3Warps * (size_t)Tc3Layout<N>::PER_WARP;
+    const size_t smem = 128 + kTc3Warps * (size_t)Tc3Layout<S, N>::PER_WARP;
     if (smem > dev.smem_per_block_optin) return KRON_ERR_NOT_SUPPORTED;
-    auto kern = tc3_kernel<N>;
+    auto kern = tc3_kernel<S, N>;
     if (!ensure_smem_optin((const void*)kern, smem)) return KRON_ERR_CUDA;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * kTc3Warps, smem) != cudaSuccess)
@@ -628,17 +650,26 @@ static kron_status launch_tc3_n(const KronDesc& d, cudaStream_t st) {
     return cudaPeekAtLastError() == cudaSuccess ? KRON_OK : KRON_ERR_CUDA;
 }
 
+template <typename S>
 static kron_status launch_tc3(const KronDesc& d, cudaStream_t st) {
-    switch (d.N) {   // even sizes: an FP32 instance is a whole number of 16-byte units
-        case 2: return launch_tc3_n<2>(d, st);
-        case 4: return launch_tc3_n<4>(d, st);
-        case 6: return launch_tc3_n<6>(d, st);
-        case 8: return launch_tc3_n<8>(d, st);
-        case 10: return launch_tc3_n<10>(d, st);
-        case 12: return launch_tc3_n<12>(d, st);
-        case 14: return launch_tc3_n<14>(d, st);
-        case 16: return launch_tc3_n<16>(d, st);
-        default: return KRON_ERR_NOT_SUPPORTED;
+    switch (d.N) {
+        case 1: return launch_tc3_n<S, 1>(d, st);
+        case 2: return launch_tc3_n<S, 2>(d, st);
+        case 3: return launch_tc3_n<S, 3>(d, st);
+        case 4: return launch_tc3_n<S, 4>(d, st);
+        case 5: return launch_tc3_n<S, 5>(d, st);
+        case 6: return launch_tc3_n<S, 6>(d, st);
+        case 7: return launch_tc3_n<S, 7>(d, st);
+        case 8: return launch_tc3_n<S, 8>(d, st);
+        case 9: return launch_tc3_n<S, 9>(d, st);
+        case 10: return launch_tc3_n<S, 10>(d, st);
+        case 11: return launch_tc3_n<S, 11>(d, st);
+        case 12: return launch_tc3_n<S, 12>(d, st);
+        case 13: return launch_tc3_n<S, 13>(d, st);
+        case 14: return launch_tc3_n<S, 14>(d, st);
+        case 15: return launch_tc3_n<S, 15>(d, st);
+        case 16: return launch_tc3_n<S, 16>(d, st);
+        default: return KRON_ERR_INVALID_VALUE;
     }
 }
 
@@ -671,13 +702,12 @@ kron_status launch_tc(const KronDesc& d, cudaStream_t st) {
         (d.D == 2 ? (d.ldy != d.N || d.ldyp != (int64_t)d.N * d.N)
                   : (d.ldy != d.N || d.ldy2 != d.N * d.N || d.ldyp != (int64_t)d.N * d.N * d.N)))
         return KRON_ERR_NOT_SUPPORTED;
-    if (d.D == 2) {
-        if (d.io == KRON_R32F) return launch_tc2<float>(d, st);
-        if (d.io == KRON_R16BF) return launch_tc2<__nv_bfloat16>(d, st);
-        return KRON_ERR_NOT_SUPPORTED;
+    switch (d.io) {
+        case KRON_R32F: return d.D == 2 ? launch_tc2<float>(d, st) : launch_tc3<float>(d, st);
+        case KRON_R16BF: return d.D == 2 ? launch_tc2<__nv_bfloat16>(d, st) : launch_tc3<__nv_bfloat16>(d, st);
+        case KRON_R16F: return d.D == 2 ? launch_tc2<__half>(d, st) : launch_tc3<__half>(d, st);
+        default: return KRON_ERR_NOT_SUPPORTED;
     }
-    if (d.io == KRON_R32F) return launch_tc3(d, st);
-    return KRON_ERR_NOT_SUPPORTED;
 }
 
 }  // namespace kron
