@@ -9,6 +9,26 @@
 
 namespace kron {
 
+// Packed float pairs for fma.rn.f32x2 (two FP32 FMAs per instruction).
+typedef unsigned long long f2;   // two packed floats, low word = first element
+
+__device__ __forceinline__ f2 f2_pack(float lo, float hi) {
+    return (f2)__float_as_uint(lo) | ((f2)__float_as_uint(hi) << 32);
+}
+__device__ __forceinline__ float f2_lo(f2 v) { return __uint_as_float((unsigned)v); }
+__device__ __forceinline__ float f2_hi(f2 v) { return __uint_as_float((unsigned)(v >> 32)); }
+
+__device__ __forceinline__ f2 ffma2(f2 a, f2 b, f2 c) {
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2 fmul2(f2 a, f2 b) {
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 // Bits of the device status word (see kron_device_status in kron.h).
 constexpr unsigned kDevErrTimeout = 1u;
 // A bounded wait gives up after this many nanoseconds of %globaltimer.

@@ -25,6 +25,8 @@
 // (Sec. 5 attributes the 3-D slowdown to it); here it never leaves the SM.
 #pragma once
 
+#include <type_traits>
+
 #include "kron_complex.cuh"
 #include "kron_device.cuh"
 #include "kron_internal.h"
@@ -84,6 +86,47 @@ __device__ __forceinline__ void contract(const T* __restrict__ M, const T (&x)[N
 #pragma unroll
         for (int i = 0; i < N; ++i) y[i] = madd(M[i + N * l], x[l], y[i]);
     }
+}
+
+// Complex FP32 y = M x on packed pairs.  An entry m = M[i, l] is read as the
+// pair (Re m, Im m) -- its storage layout -- and x_l = (a, b) enters as the
+// duplicated pairs (a, a) and (b, b).  Two accumulators per output,
+//   P_i = sum_l (Re m * a, Im m * a),   Q_i = sum_l (Re m * b, Im m * b),
+// give y_i = (P_i.re - Q_i.im, P_i.im + Q_i.re): the four real FMAs of each
+// complex product in two fma.rn.f32x2, with the coefficients of one table.
+template <int N>
+__device__ __forceinline__ void contract_c32(const cf32* __restrict__ M, const cf32 (&x)[N], cf32 (&y)[N]) {
+    const f2* Mp = reinterpret_cast<const f2*>(M);
+    f2 P[N], Q[N];
+    {
+        const f2 a = f2_pack(x[0].re, x[0].re), b = f2_pack(x[0].im, x[0].im);
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            P[i] = fmul2(Mp[i], a);
+            Q[i] = fmul2(Mp[i], b);
+        }
+    }
+#pragma unroll
+    for (int l = 1; l < N; ++l) {
+        const f2 a = f2_pack(x[l].re, x[l].re), b = f2_pack(x[l].im, x[l].im);
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            P[i] = ffma2(Mp[i + N * l], a, P[i]);
+            Q[i] = ffma2(Mp[i + N * l], b, Q[i]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) y[i] = cf32(f2_lo(P[i]) - f2_hi(Q[i]), f2_hi(P[i]) + f2_lo(Q[i]));
+}
+
+// Mode-K contraction of one fiber with the component of the kernel's arguments.
+template <int K, typename T, int N, int D>
+__device__ __forceinline__ void contract_mode(const FiberArgs<T, N, D>& a, const T (&x)[N], T (&y)[N]) {
+    const T* M = K == 1 ? a.m1 : K == 2 ? a.m2 : a.m3;
+    if constexpr (std::is_same<T, cf32>::value)
+        contract_c32<N>(M, x, y);
+    else
+        contract<N, T>(M, x, y);
 }
 
 // Byte span of tile `tile` of a contiguous batch.  The bulk copy takes the
@@ -209,8 +252,13 @@ __device__ __forceinline__ void store_fiber(const FiberArgs<T, N, D>& a, S* dst,
         if (i < a.ye1) dst[i] = o[i];
 }
 
+// Complex FP32 at 2-D holds two accumulators per output; three CTAs per SM
+// (the shared-memory limit of the 2-D tiles) cap it at 85 registers.
+template <typename T, int D>
+constexpr int fiber_min_blocks() { return std::is_same<T, cf32>::value && D == 2 ? 3 : 1; }
+
 template <typename T, typename S, int N, int D>
-__global__ void __launch_bounds__(kFiberThreads)
+__global__ void __launch_bounds__(kFiberThreads, fiber_min_blocks<T, D>())
 fiber_kernel(const __grid_constant__ FiberArgs<T, N, D> a) {
     using L = FiberLayout<N, D>;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -276,7 +324,7 @@ fiber_kernel(const __grid_constant__ FiberArgs<T, N, D> a) {
                 T x[N], w[N];
 #pragma unroll
                 for (int m = 0; m < N; ++m) x[m] = load_cvt<T, S>(xr[N * m]);
-                contract<N, T>(a.m2, x, w);
+                contract_mode<2>(a, x, w);
                 T* wr = ex1 + q * L::SUQ + l;
 #pragma unroll
                 for (int j = 0; j < N; ++j) wr[(N + 1) * j] = w[j];
@@ -290,7 +338,7 @@ fiber_kernel(const __grid_constant__ FiberArgs<T, N, D> a) {
                 T x[N], t[N];
 #pragma unroll
                 for (int p = 0; p < N; ++p) x[p] = load_cvt<T, S>(xr[N * N * p]);
-                contract<N, T>(a.m3, x, t);
+                contract_mode<3>(a, x, t);
                 T* tr = ex1 + q * L::STQ + i + N * j;
 #pragma unroll
                 for (int k = 0; k < N; ++k) tr[L::ST * k] = t[k];
@@ -323,7 +371,7 @@ fiber_kernel(const __grid_constant__ FiberArgs<T, N, D> a) {
                 T w[N], y[N];
 #pragma unroll
                 for (int l = 0; l < N; ++l) w[l] = wr[l];
-                contract<N, T>(a.m1, w, y);
+                contract_mode<1>(a, w, y);
                 if (j < a.ye2) store_fiber<T, S, N, D>(a, Y + (inst0 + q) * a.ldyp + (int64_t)a.ldy * j, y);
             }
             __syncthreads();   // W is rewritten by the next tile's first stage
@@ -336,7 +384,7 @@ fiber_kernel(const __grid_constant__ FiberArgs<T, N, D> a) {
                 T t[N], u[N];
 #pragma unroll
                 for (int m = 0; m < N; ++m) t[m] = tr[N * m];
-                contract<N, T>(a.m2, t, u);
+                contract_mode<2>(a, t, u);
                 T* ur = ex2 + q * L::SUQ + i + L::SU * k;
 #pragma unroll
                 for (int j = 0; j < N; ++j) ur[(N + 1) * j] = u[j];
@@ -349,7 +397,7 @@ fiber_kernel(const __grid_constant__ FiberArgs<T, N, D> a) {
                 T u[N], y[N];
 #pragma unroll
                 for (int l = 0; l < N; ++l) u[l] = ur[l];
-                contract<N, T>(a.m1, u, y);
+                contract_mode<1>(a, u, y);
                 if (j < a.ye2 && k < a.ye3)
                     store_fiber<T, S, N, D>(
                         a, Y + (inst0 + q) * a.ldyp + (int64_t)a.ldy * j + (int64_t)a.ldy2 * k, y);

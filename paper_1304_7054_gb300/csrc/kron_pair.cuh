@@ -25,25 +25,6 @@
 
 namespace kron {
 
-typedef unsigned long long f2;   // two packed floats, low word = first element
-
-__device__ __forceinline__ f2 f2_pack(float lo, float hi) {
-    return (f2)__float_as_uint(lo) | ((f2)__float_as_uint(hi) << 32);
-}
-__device__ __forceinline__ float f2_lo(f2 v) { return __uint_as_float((unsigned)v); }
-__device__ __forceinline__ float f2_hi(f2 v) { return __uint_as_float((unsigned)(v >> 32)); }
-
-__device__ __forceinline__ f2 ffma2(f2 a, f2 b, f2 c) {
-    f2 d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-__device__ __forceinline__ f2 fmul2(f2 a, f2 b) {
-    f2 d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-
 // Two adjacent storage elements as a float pair.
 template <typename S> __device__ __forceinline__ f2 load_pair(const S* p);
 template <> __device__ __forceinline__ f2 load_pair<float>(const float* p) {
