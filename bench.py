@@ -549,7 +549,7 @@ def kernel_of(kind, n, io, compute, variant="auto"):
     if variant == "exchange":
         return f"pair_kernel<{io},n={n},{kind}-D>"
     if kind == 2 and n == 16 and io == "f32":
-        return "pair16_kernel<f32,n=16,2-D>"
+        return "pair16t_kernel<f32,n=16,2-D>"
     if kind == 2 and n == 16 and io in ("bf16", "f16"):
         return f"pair16h_kernel<{io},n=16,2-D>"
     if kind == 2 and n in (10, 14) and io == "f32":

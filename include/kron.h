@@ -223,8 +223,8 @@ KRON_API kron_status kron_device_status(kron_stream_t stream);
 
 /*
  * kron_set_first_wait_limit_ns -- a test aid for the failure path, off by
- * default (0).  With ns > 0, the first operand wait of every CTA of later
- * launches of the 2-D n = 16 FP32 kernel (kron2_batched, contiguous FP32
+ * default (0).  With ns > 0, the first operand wait of every CTA (of every
+ * compute group of a CTA) of later launches of the 2-D n = 16 FP32 kernel (kron2_batched, contiguous FP32
  * batches, n = 16) polls for at most ns nanoseconds instead of the normal
  * limit.  A limit shorter than an operand copy takes to land makes that real
  * wait expire on a normal launch: the kernel records the expiry in the device
@@ -264,8 +264,8 @@ KRON_API kron_status kron_peak_probe(kron_stream_t stream, int unit, int iters, 
  * read at first use; later lines override earlier ones), and returns it.
  *
  * For contiguous batches the tile size also chooses the kernel: the in-place
- * kernels take their own tile shapes (2-D n = 16, any storage: 16 instances;
- * the rest FP32 only: 2-D
+ * kernels take their own tile shapes (2-D n = 16: FP32 8, 16, 24 or 32
+ * instances, 16-bit storage 16; the rest FP32 only: 2-D
  * n = 10, 14: multiples of 8; 3-D n = 16: 1; 3-D n = 10, 14: 4; odd n: multiples
  * of 4), and any other tile size runs the generic kernel of that shape.  Every
  * configuration computes the same result within the documented tolerance.
@@ -295,9 +295,18 @@ KRON_API kron_status kron_autotune(kron_stream_t stream, int kind, int n, int64_
  *   fibers_per_step:    register blocking of the last contraction of the
  *                       packed-pair bodies: 1 or 2 fibers per thread and step
  *                       (0 = default)
+ *   compute_warps:      compute warps per CTA (0 = default).  Only the FP32
+ *                       2-D n = 16 in-place body takes it: its warps work in
+ *                       groups of instances_per_tile / 4, each group on its
+ *                       own tile of the ring, so compute_warps must be a
+ *                       multiple of that, at most 16.  With pipeline_depth
+ *                       (up to 12 tiles for that body, 8 for the others) it
+ *                       sets the split of an SM between registers (resident
+ *                       warps) and shared memory (tiles in flight).
  *
  * kron_set_kernel_config returns KRON_ERR_NOT_SUPPORTED when the body does not
- * exist for (kind, n, io, comp) (in place: 2-D n = 16 any storage, FP32 2-D n =
+ * exist for (kind, n, io, comp) (in place: 2-D n = 16 any storage -- FP32 with
+ * tiles of 8, 16, 24 or 32 instances, 16-bit with 16 --, FP32 2-D n =
  * 10, 14, FP32 3-D n = 10, 14, 16, FP32 odd n; exchange: even n, FP32 or 16-bit
  * storage; scalar: every real storage type) and KRON_ERR_INVALID_VALUE for
  * values out of range; all-zero restores the built-in default.  Strided,
@@ -325,6 +334,7 @@ typedef struct {
     int instances_per_tile;
     int pipeline_depth;
     int fibers_per_step;
+    int compute_warps;
 } kron_kernel_config;
 
 KRON_API kron_status kron_set_kernel_config(int kind, int n, kron_dtype io, kron_compute comp,

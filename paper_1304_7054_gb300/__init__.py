@@ -318,20 +318,21 @@ VARIANTS = {"auto": 0, "in_place": 1, "exchange": 2, "scalar": 3}
 
 
 class KernelConfig(ctypes.Structure):
-    """kron_kernel_config: kernel body, instances per tile, pipeline depth and
-    fibers per step of one fixed-size (kind, n, storage, compute)."""
+    """kron_kernel_config: kernel body, instances per tile, pipeline depth,
+    fibers per step and compute warps of one fixed-size (kind, n, storage, compute)."""
     _fields_ = [("variant", ctypes.c_int), ("instances_per_tile", ctypes.c_int), ("pipeline_depth", ctypes.c_int),
-                ("fibers_per_step", ctypes.c_int)]
+                ("fibers_per_step", ctypes.c_int), ("compute_warps", ctypes.c_int)]
 
     def as_dict(self):
         names = {v: k for k, v in VARIANTS.items()}
         return {"variant": names.get(self.variant, self.variant), "instances_per_tile": self.instances_per_tile,
-                "pipeline_depth": self.pipeline_depth, "fibers_per_step": self.fibers_per_step}
+                "pipeline_depth": self.pipeline_depth, "fibers_per_step": self.fibers_per_step,
+                "compute_warps": self.compute_warps}
 
 
 def set_kernel_config(kind, n, io, compute="native", variant="auto", instances_per_tile=0, pipeline_depth=0,
-                      fibers_per_step=0):
-    c = KernelConfig(VARIANTS[variant], instances_per_tile, pipeline_depth, fibers_per_step)
+                      fibers_per_step=0, compute_warps=0):
+    c = KernelConfig(VARIANTS[variant], instances_per_tile, pipeline_depth, fibers_per_step, compute_warps)
     _check(load_library().kron_set_kernel_config(kind, n, DTYPES[io], COMPUTE[compute], ctypes.byref(c)),
            "kron_set_kernel_config")
 

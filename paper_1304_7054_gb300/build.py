@@ -79,6 +79,7 @@ FAMILY_SOURCES = {
     "pair_kernel": ["kron_pair.cuh", "kron_fiber.cuh", "kron_device.cuh"],
     "pair16_kernel": ["kron_pair16.cu", "kron_pair.cuh", "kron_fiber.cuh", "kron_device.cuh"],
     "pair16h_kernel": ["kron_pair16.cu", "kron_pair.cuh", "kron_fiber.cuh", "kron_device.cuh"],
+    "pair16t_kernel": ["kron_pair16.cu", "kron_pair.cuh", "kron_fiber.cuh", "kron_device.cuh", "kron_internal.h"],
     "pair2ip_kernel": ["kron_pair2ip.cu", "kron_pair.cuh", "kron_fiber.cuh", "kron_device.cuh"],
     "pair3ip_kernel": ["kron_pair3ip.cu", "kron_pair.cuh", "kron_fiber.cuh", "kron_device.cuh"],
     "pair3pk_kernel": ["kron_pair3ip.cu", "kron_pair.cuh", "kron_fiber.cuh", "kron_device.cuh"],

@@ -47,6 +47,7 @@ struct KronDesc {
     int grid = 0;        // CTAs; 0 = persistent (all resident CTAs)
     int variant = 0;     // kernel body (kron_variant); 0 = built-in choice
     int fps = 0;         // fibers per step of the last contraction; 0 = default
+    int warps = 0;       // compute warps per CTA (bodies that take it); 0 = default
 };
 
 size_t elem_size(kron_dtype t);
@@ -96,6 +97,10 @@ kron_status launch_pair_f16_d3(const KronDesc& d, cudaStream_t s);
 // 2-D n = 16 FP32 pair kernel with the exchange in place in the operand tile
 // (contiguous X and Y, 16 instances per tile); KRON_ERR_NOT_SUPPORTED otherwise.
 kron_status launch_pair16(const KronDesc& d, cudaStream_t s);
+// FP32 2-D n = 16 tensor-copy body: default tile, most compute warps, deepest ring.
+constexpr int kPair16TDefaultP = 16;
+constexpr int kPair16TMaxWarps = 16;
+constexpr int kPair16TMaxRing = 12;
 // 2-D n = 10, 14 FP32 pair kernels with the exchange in place (tiles of a
 // multiple of 8 instances); KRON_ERR_NOT_SUPPORTED otherwise.
 kron_status launch_pair2ip(const KronDesc& d, cudaStream_t s);

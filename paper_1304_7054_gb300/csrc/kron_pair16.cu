@@ -24,6 +24,11 @@
 //    way, both with an L2 evict-first policy (the data is streamed once); the
 //    four compute warps never issue a global memory access (except the reads
 //    of Y that beta != 0 needs).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 #include "kron_pair.cuh"
 
 namespace kron {
@@ -192,6 +197,220 @@ __global__ void __launch_bounds__(kThreads, 6) pair16_kernel(const __grid_consta
 size_t pair16_smem_bytes(int nb) { return 128 + (size_t)nb * kTileWords * sizeof(float); }
 
 // ---------------------------------------------------------------------------
+// FP32, tiles moved by 3-D tensor copies (pair16t_kernel).  The same two
+// contractions; a tile of P instances (P a multiple of 8) arrives and leaves
+// by ONE tensor copy (cp.async.bulk.tensor) each way instead of one bulk copy
+// per instance.  X and Y are described to the copy engine as 16 x 16 x batch
+// arrays and the box is 20 x 17 x P: rows 16..19 and column 16 lie outside
+// the array, so the loads fill them with zeros and the stores skip them, and
+// in shared memory
+//   element (i, j) of instance q sits at word i + 20 j + 340 q.
+// A column stride of 20 words puts the 8 columns of a quarter-warp's 16-byte
+// accesses on 8 distinct 4-bank groups (20 j mod 32 = 0, 20, 8, 28, 16, 4,
+// 24, 12), and instances q and q + 4 lie 1360 = 16 (mod 32) words apart.  A
+// warp owns the four instances {A, A+1, A+4, A+5} (A = 8 G + 2 u) through both
+// stages, so the stages are separated by __syncwarp:
+//   stage 1: lane (h, t) takes rows (2t, 2t+1) of instance A + (lane >> 4) +
+//            4 h, h = (lane >> 3) & 1; a half-warp reads instances q and q + 4
+//            with 8-byte accesses: 32 distinct banks.
+//   stage 2: two passes, lanes 0-15 on instance A (then A + 4), lanes 16-31 on
+//            A + 1 (A + 5), column j = lane & 15.
+// Instances past the end of the batch are zero-filled by the load and skipped
+// by the store, so the last tile needs no guard (except for beta's reads).
+// ---------------------------------------------------------------------------
+constexpr int kTRows = 20, kTCols = 17;
+constexpr int kTInst = kTRows * kTCols;     // 340 words per instance
+constexpr int kTMaxWarps = kPair16TMaxWarps;   // compute warps per CTA
+constexpr int kTMaxRing = kPair16TMaxRing;
+
+struct Pair16TArgs {   // 128-byte aligned (CUtensorMap)
+    CUtensorMap tx, ty;                     // X, Y as 16 x 16 x batch FP32 arrays
+    PairArgs<kN, 2> a;
+    int groups;                             // compute groups of P / 4 warps; group g takes tiles it = g mod groups
+};
+
+__device__ __forceinline__ void tensor_load3(void* dst, const CUtensorMap* tm, int c2, uint64_t* bar, uint64_t pol) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(smem_u32(dst)),
+        "l"((unsigned long long)tm), "r"(0), "r"(0), "r"(c2), "r"(smem_u32(bar)), "l"(pol)
+        : "memory");
+}
+__device__ __forceinline__ void tensor_store3(const CUtensorMap* tm, int c2, const void* src, uint64_t pol) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group.L2::cache_hint [%0, {%1, %2, %3}], [%4], %5;" ::
+                     "l"((unsigned long long)tm), "r"(0), "r"(0), "r"(c2), "r"(smem_u32(src)), "l"(pol)
+                 : "memory");
+}
+
+// bar.red.or over the `nthreads` threads that use named barrier `id`.
+__device__ __forceinline__ bool sync_or_n(bool v, int id, int nthreads) {
+    unsigned r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "bar.red.or.pred p, %2, %3, q;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(r)
+        : "r"((unsigned)v), "r"(id), "r"(nthreads)
+        : "memory");
+    return r != 0;
+}
+
+__global__ void __launch_bounds__(32 * (kTMaxWarps + 1), 1) pair16t_kernel(const __grid_constant__ Pair16TArgs ta) {
+    const PairArgs<kN, 2>& a = ta.a;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem);
+    uint64_t* empty = full + kTMaxRing;
+    float* ring = reinterpret_cast<float*>(smem + 256);
+    const int NB = a.nstage;
+    const int P = a.P;
+    const int gwarps = P / 4;                  // warps of one compute group
+    const int ncompute = 32 * gwarps * ta.groups;
+    const int tileWords = P * kTInst;
+    const unsigned tileBytes = (unsigned)tileWords * 4u;
+    const int tid = threadIdx.x;
+    const int ntiles = (int)((a.batch + P - 1) / P);
+    const int grid = gridDim.x;
+
+    if (tid == 0) {
+        for (int s = 0; s < NB; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 32 * gwarps);
+        }
+        fence_barrier_init();
+    }
+    __syncthreads();
+
+    if (tid >= ncompute) {
+        // Producer (one thread): tile `it` into buffer it % NB once the compute
+        // warps released the buffer's previous tile, whose results leave first.
+        if (tid != ncompute) return;
+        const uint64_t pol = l2_evict_first_policy();
+        int it = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += grid, ++it) {
+            const int s = it % NB;
+            float* buf = ring + s * tileWords;
+            if (it >= NB) {
+                if (!mbar_wait_bounded(&empty[s], (unsigned)(it / NB - 1) & 1u, a.err)) {
+                    bulk_wait_all();
+                    return;
+                }
+                tensor_store3(&ta.ty, (tile - NB * grid) * P, buf, pol);
+                bulk_commit();
+                bulk_wait_read();   // the results have left the buffer
+            }
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&full[s], tileBytes);
+            tensor_load3(buf, &ta.tx, tile * P, &full[s], pol);
+        }
+        for (int j = it > NB ? it - NB : 0; j < it; ++j) {   // the last tiles' results
+            if (!mbar_wait_bounded(&empty[j % NB], (unsigned)(j / NB) & 1u, a.err)) break;
+            tensor_store3(&ta.ty, (blockIdx.x + j * grid) * P, ring + (j % NB) * tileWords, pol);
+            bulk_commit();
+        }
+        bulk_wait_all();
+        return;
+    }
+
+    const f2* m1p = reinterpret_cast<const f2*>(a.m1);
+    const float* Yg = static_cast<const float*>(a.Y);
+    const int gidx = (tid >> 5) / gwarps;
+    const int warp = (tid >> 5) - gidx * gwarps, lane = tid & 31;
+    const int A = 8 * (warp >> 1) + 2 * (warp & 1);          // the warp's instances: A, A+1, A+4, A+5
+    const int q1 = A + (lane >> 4) + 4 * ((lane >> 3) & 1);   // stage 1
+    const int t1 = 2 * (lane & 7);
+    const int j2 = lane & 15;                                 // stage 2
+    const int G = ta.groups;
+    for (int it = gidx, tile = blockIdx.x + gidx * grid; tile < ntiles; it += G, tile += G * grid) {
+        const int s = it % NB;
+        float* buf = ring + s * tileWords;
+        const int64_t inst0 = (int64_t)tile * P;
+        const int cnt = (int)min((int64_t)P, a.batch - inst0);
+        const bool ok = (it < G && a.first_wait_ns)
+                            ? mbar_wait_polled(&full[s], (unsigned)(it / NB) & 1u, a.err, a.first_wait_ns)
+                            : mbar_wait_bounded(&full[s], (unsigned)(it / NB) & 1u, a.err);
+        if (sync_or_n(!ok, 1 + gidx, 32 * gwarps)) {
+            // A copy did not land in time: wait (bounded) for the ones that may still
+            // be in flight into this CTA's buffers, then give up.
+            if (warp == 0 && lane == 0)
+                for (int j = it; j < it + NB; ++j)
+                    if (blockIdx.x + j * grid < ntiles)
+                        mbar_wait_bounded(&full[j % NB], (unsigned)(j / NB) & 1u, a.err);
+            return;
+        }
+        // ---- stage 1: rows (t1, t1+1) of instance q1 times M2^T, in place ----
+        {
+            float* p = buf + q1 * kTInst + t1;
+            f2 x[kN];
+#pragma unroll
+            for (int m = 0; m < kN; ++m) x[m] = *reinterpret_cast<const f2*>(p + kTRows * m);
+            f2 w[kN];
+            contract_dup<kN>(a.da, x, w);
+#pragma unroll
+            for (int j = 0; j < kN; ++j) *reinterpret_cast<f2*>(p + kTRows * j) = w[j];
+        }
+        __syncwarp();
+        // ---- stage 2: column j2 of W times M1, in place; two instances per pass ----
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+            const int q = A + (lane >> 4) + 4 * h;
+            float* col = buf + q * kTInst + kTRows * j2;
+            float w[kN];
+            load_col(col, w);
+            f2 y[kN / 2];
+            contract_rows<kN>(m1p, w, y);
+            if (!a.alpha_one) {
+                const f2 al = f2_pack(a.alpha, a.alpha);
+#pragma unroll
+                for (int r = 0; r < kN / 2; ++r) y[r] = fmul2(y[r], al);
+            }
+            if (!a.beta_zero && q < cnt) {
+                const f2 be = f2_pack(a.beta, a.beta);
+                const float* yg = Yg + (inst0 + q) * kNX + kN * j2;
+#pragma unroll
+                for (int r = 0; r < kN / 2; ++r) y[r] = ffma2(be, load_pair<float>(yg + 2 * r), y[r]);
+            }
+#pragma unroll
+            for (int c = 0; c < kN / 4; ++c)
+                *reinterpret_cast<uint4*>(col + 4 * c) = make_uint4(
+                    (unsigned)y[2 * c], (unsigned)(y[2 * c] >> 32), (unsigned)y[2 * c + 1], (unsigned)(y[2 * c + 1] >> 32));
+        }
+        fence_proxy_async_smem();   // results written: visible to the tensor store
+        mbar_arrive(&empty[s]);
+    }
+}
+
+size_t pair16t_smem_bytes(int P, int nb) { return 256 + (size_t)nb * P * kTInst * sizeof(float); }
+
+// cuTensorMapEncodeTiled from the driver, looked up once.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// X or Y as a 16 x 16 x batch FP32 array, copied in boxes of 20 x 17 x P.
+bool encode_inst_map(CUtensorMap* m, const void* base, int64_t batch, int P) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[3] = {16, 16, (cuuint64_t)batch};
+    const cuuint64_t strides[2] = {16 * sizeof(float), 256 * sizeof(float)};
+    const cuuint32_t box[3] = {kTRows, kTCols, (cuuint32_t)P};
+    const cuuint32_t es[3] = {1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// ---------------------------------------------------------------------------
 // 16-bit storage (bf16, f16), FP32 arithmetic.  W (FP32) cannot overwrite a
 // 16-bit operand, so it has its own buffer -- laid out as the FP32 kernel's
 // tile, conflict-free -- while the results overwrite the dead operand slots
@@ -335,8 +554,14 @@ size_t pair16h_smem_bytes(int nb) { return 128 + (size_t)nb * kHTileBytes + kHWB
 // Tile sizes other than 16 instances are left to the generic pair kernel.
 kron_status launch_pair16(const KronDesc& d, cudaStream_t st) {
     if (d.D != 2 || d.N != kN || d.io == KRON_R64F || d.comp != KRON_COMPUTE_NATIVE || !d.contiguous ||
-        !d.ycontig || (d.P > 0 && d.P != kTileP))
+        !d.ycontig)
         return KRON_ERR_NOT_SUPPORTED;
+    // FP32: the tensor-copy body (tiles of 8, 16, 24 or 32 instances); the slot
+    // body below serves 16-bit storage, and FP32 where tensor maps cannot
+    // describe the batch (2^31 instances or more) or are unavailable.
+    const bool tens = d.io == KRON_R32F && d.batch < (1ll << 31) - 64 &&
+                      (d.P <= 0 || (d.P % 8 == 0 && d.P <= 32));
+    if (!tens && d.P > 0 && d.P != kTileP) return KRON_ERR_NOT_SUPPORTED;
     const DeviceInfo& dev = device_info();
     if (dev.sms <= 0) return KRON_ERR_CUDA;
     PairArgs<kN, 2> a;
@@ -361,6 +586,45 @@ kron_status launch_pair16(const KronDesc& d, cudaStream_t st) {
     a.err = device_error_word();
     if (!a.err) return KRON_ERR_CUDA;
     a.first_wait_ns = d.io == KRON_R32F ? first_wait_limit_ns() : 0;
+    if (tens) {
+        Pair16TArgs ta;
+        // Measured default: 16-instance tiles, an eight-deep ring and four groups
+        // of four compute warps -- one CTA per SM holding 170 KB of tiles.
+        const int P = d.P > 0 ? d.P : kPair16TDefaultP;
+        if (encode_inst_map(&ta.tx, d.X, d.batch, P) && encode_inst_map(&ta.ty, d.Y, d.batch, P)) {
+            const int warps = d.warps > 0 ? d.warps : kPair16TMaxWarps;
+            const int groups = warps / (P / 4);
+            if (groups < 1 || warps % (P / 4) || warps > kTMaxWarps) return KRON_ERR_NOT_SUPPORTED;
+            ta.groups = groups;
+            int nb = d.nstage >= 1 ? d.nstage : 2 * groups;
+            if (nb > kTMaxRing) nb = kTMaxRing;
+            if (nb < groups) nb = groups;
+            size_t smem = pair16t_smem_bytes(P, nb);
+            while (nb > 1 && smem > dev.smem_per_block_optin) smem = pair16t_smem_bytes(P, --nb);
+            if (smem > dev.smem_per_block_optin) return KRON_ERR_NOT_SUPPORTED;
+            a.P = P;
+            a.nstage = nb;
+            ta.a = a;
+            const void* kern = (const void*)pair16t_kernel;
+            if (!ensure_smem_optin(kern, smem)) return KRON_ERR_CUDA;
+            const int threads = 32 * (groups * (P / 4) + 1);
+            const int64_t ntiles = (d.batch + P - 1) / P;
+            int64_t grid = d.grid;
+            if (grid <= 0) {
+                int per_sm = 0;
+                if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) != cudaSuccess)
+                    return KRON_ERR_CUDA;
+                grid = (int64_t)(per_sm < 1 ? 1 : per_sm) * dev.sms;
+            }
+            if (grid > ntiles) grid = ntiles;
+            if (grid < 1) grid = 1;
+            void* args[] = {&ta};
+            if (cudaLaunchKernel(kern, dim3((unsigned)grid), dim3(threads), args, smem, st) != cudaSuccess)
+                return KRON_ERR_CUDA;
+            return cudaPeekAtLastError() == cudaSuccess ? KRON_OK : KRON_ERR_CUDA;
+        }
+        if (d.P > 0 && d.P != kTileP) return KRON_ERR_NOT_SUPPORTED;
+    }
     a.P = kTileP;
     // FP32: one buffer per CTA (measured best: the six to seven resident CTAs
     // per SM overlap one another's copies; a second buffer costs resident CTAs).

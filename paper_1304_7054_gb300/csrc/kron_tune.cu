@@ -1,13 +1,14 @@
 // Kernel-configuration table and autotuner for the fixed-size kernels.
 //
-// A configuration is (kernel body, instances per tile, bulk-copy pipeline depth,
-// fibers per step of the last contraction) for one (kind, n, storage type,
-// compute mode).  kron_autotune_config times the candidates on the caller's
-// buffers with CUDA events and keeps the fastest; the table can be persisted in
-// a small text file named by the KRON_TUNE_CACHE environment variable (one line
-// per entry: device-key kind n io comp P depth variant fps, the key being GPU
-// name, SM count and driver version; a later line overrides an earlier one and
-// all zeros mean the built-in default), read at first use.
+// A configuration is (kernel body, instances per tile, bulk-copy pipeline
+// depth, fibers per step of the last contraction, compute warps per CTA) for
+// one (kind, n, storage type, compute mode).  kron_autotune_config times the
+// candidates on the caller's buffers with CUDA events and keeps the fastest;
+// the table can be persisted in a small text file named by the KRON_TUNE_CACHE
+// environment variable (one line per entry: device-key kind n io comp P depth
+// variant fps warps, the key being GPU name, SM count and driver version; a
+// later line overrides an earlier one and all zeros mean the built-in default),
+// read at first use.
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -26,7 +27,7 @@ namespace kron {
 namespace {
 
 using Key = std::tuple<int, int, int, int>;   // kind, n, io, comp
-struct Entry { int P, nstage, variant, fps; };
+struct Entry { int P, nstage, variant, fps, warps; };
 
 std::mutex g_mu;
 std::map<Key, Entry> g_table;
@@ -55,13 +56,14 @@ void load_cache_locked() {
     const std::string me = device_key();
     char line[512], name[256];
     while (fgets(line, sizeof(line), f)) {
-        int kind, n, io, comp, P, ns, var = 0, fps = 0;
-        const int got = sscanf(line, "%255s %d %d %d %d %d %d %d %d", name, &kind, &n, &io, &comp, &P, &ns, &var, &fps);
+        int kind, n, io, comp, P, ns, var = 0, fps = 0, warps = 0;
+        const int got = sscanf(line, "%255s %d %d %d %d %d %d %d %d %d", name, &kind, &n, &io, &comp, &P, &ns, &var,
+                               &fps, &warps);
         if (got < 7 || me != name) continue;
-        if (P == 0 && ns == 0 && var == 0 && fps == 0)
+        if (P == 0 && ns == 0 && var == 0 && fps == 0 && warps == 0)
             g_table.erase(Key(kind, n, io, comp));   // a later tuning kept the default
         else
-            g_table[Key(kind, n, io, comp)] = Entry{P, ns, var, fps};
+            g_table[Key(kind, n, io, comp)] = Entry{P, ns, var, fps, warps};
     }
     fclose(f);
 }
@@ -71,8 +73,8 @@ void append_cache(const Key& k, const Entry& e) {
     if (!path || !*path) return;
     FILE* f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "%s %d %d %d %d %d %d %d %d\n", device_key().c_str(), std::get<0>(k), std::get<1>(k), std::get<2>(k),
-            std::get<3>(k), e.P, e.nstage, e.variant, e.fps);
+    fprintf(f, "%s %d %d %d %d %d %d %d %d %d\n", device_key().c_str(), std::get<0>(k), std::get<1>(k), std::get<2>(k),
+            std::get<3>(k), e.P, e.nstage, e.variant, e.fps, e.warps);
     fclose(f);
 }
 
@@ -85,7 +87,8 @@ bool variant_ok(int kind, int n, kron_dtype io, kron_compute comp, int variant, 
     const bool f32 = io == KRON_R32F, half = io == KRON_R16BF || io == KRON_R16F;
     switch (variant) {
         case KRON_VARIANT_IN_PLACE:
-            if (kind == 2 && n == 16 && (f32 || half)) return P == 0 || P == 16;
+            if (kind == 2 && n == 16 && f32) return P == 0 || P == 16 || P == 24 || P == 32 || P == 8;
+            if (kind == 2 && n == 16 && half) return P == 0 || P == 16;
             if (!f32) return false;
             if (kind == 2 && (n == 10 || n == 14)) return P % 8 == 0;
             if (kind == 3 && n == 16) return P <= 1;
@@ -96,6 +99,29 @@ bool variant_ok(int kind, int n, kron_dtype io, kron_compute comp, int variant, 
         case KRON_VARIANT_SCALAR: return true;
         default: return false;
     }
+}
+
+// Whether `warps` compute warps per CTA fit the body (0: its default).  Only the
+// FP32 2-D n = 16 in-place body takes it: groups of P / 4 warps, at most 16.
+bool warps_ok(int kind, int n, kron_dtype io, kron_compute comp, int variant, int P, int warps) {
+    if (warps == 0) return true;
+    if (kind != 2 || n != 16 || io != KRON_R32F || comp != KRON_COMPUTE_NATIVE) return false;
+    if (variant != KRON_VARIANT_AUTO && variant != KRON_VARIANT_IN_PLACE) return false;
+    const int g = (P > 0 ? P : kPair16TDefaultP) / 4;
+    return warps <= kPair16TMaxWarps && warps % g == 0;
+}
+
+Entry entry_of(const kron_kernel_config& c) {
+    return Entry{c.instances_per_tile, c.pipeline_depth, c.variant, c.fibers_per_step, c.compute_warps};
+}
+bool is_default(const Entry& e) { return !e.P && !e.nstage && !e.variant && !e.fps && !e.warps; }
+
+// Stores e for key k (all zero: removes the entry, i.e. the built-in default).
+void put_locked(const Key& k, const Entry& e) {
+    if (is_default(e))
+        g_table.erase(k);
+    else
+        g_table[k] = e;
 }
 
 }  // namespace
@@ -109,12 +135,13 @@ void apply_tile_config(KronDesc& d) {
         if (d.nstage < 0) d.nstage = it->second.nstage > 0 ? it->second.nstage : -1;
         d.variant = it->second.variant;
         d.fps = it->second.fps;
+        d.warps = it->second.warps;
     }
 }
 
 void tune_cache_append(int kind, int n, kron_dtype io, kron_compute comp, int P, int nstage) {
     std::lock_guard<std::mutex> lock(g_mu);
-    append_cache(Key(kind, n, (int)io, (int)comp), Entry{P, nstage, 0, 0});
+    append_cache(Key(kind, n, (int)io, (int)comp), Entry{P, nstage, 0, 0, 0});
 }
 
 }  // namespace kron
@@ -126,17 +153,16 @@ extern "C" {
 KRON_API kron_status kron_set_kernel_config(int kind, int n, kron_dtype io, kron_compute comp,
                                             const kron_kernel_config* c) {
     if (!c || (kind != 2 && kind != 3) || n < 1 || n > kMaxN || c->instances_per_tile < 0 ||
-        c->instances_per_tile > 4096 || c->pipeline_depth < 0 || c->pipeline_depth > 8 || c->fibers_per_step < 0 ||
-        c->fibers_per_step > 2 || c->variant < 0 || c->variant > KRON_VARIANT_SCALAR)
+        c->instances_per_tile > 4096 || c->pipeline_depth < 0 || c->pipeline_depth > kPair16TMaxRing ||
+        c->fibers_per_step < 0 || c->fibers_per_step > 2 || c->variant < 0 || c->variant > KRON_VARIANT_SCALAR ||
+        c->compute_warps < 0 || c->compute_warps > kPair16TMaxWarps)
         return KRON_ERR_INVALID_VALUE;
-    if (!variant_ok(kind, n, io, comp, c->variant, c->instances_per_tile)) return KRON_ERR_NOT_SUPPORTED;
+    if (!variant_ok(kind, n, io, comp, c->variant, c->instances_per_tile) ||
+        !warps_ok(kind, n, io, comp, c->variant, c->instances_per_tile, c->compute_warps))
+        return KRON_ERR_NOT_SUPPORTED;
     std::lock_guard<std::mutex> lock(g_mu);
     load_cache_locked();
-    if (c->instances_per_tile == 0 && c->pipeline_depth == 0 && c->variant == 0 && c->fibers_per_step == 0)
-        g_table.erase(Key(kind, n, (int)io, (int)comp));
-    else
-        g_table[Key(kind, n, (int)io, (int)comp)] =
-            Entry{c->instances_per_tile, c->pipeline_depth, c->variant, c->fibers_per_step};
+    put_locked(Key(kind, n, (int)io, (int)comp), entry_of(*c));
     return KRON_OK;
 }
 
@@ -145,11 +171,12 @@ KRON_API kron_status kron_get_kernel_config(int kind, int n, kron_dtype io, kron
     std::lock_guard<std::mutex> lock(g_mu);
     load_cache_locked();
     auto it = g_table.find(Key(kind, n, (int)io, (int)comp));
-    const Entry e = it == g_table.end() ? Entry{0, 0, 0, 0} : it->second;
+    const Entry e = it == g_table.end() ? Entry{0, 0, 0, 0, 0} : it->second;
     c->variant = e.variant;
     c->instances_per_tile = e.P;
     c->pipeline_depth = e.nstage;
     c->fibers_per_step = e.fps;
+    c->compute_warps = e.warps;
     return KRON_OK;
 }
 
@@ -160,10 +187,7 @@ KRON_API kron_status kron_set_tile_config(int kind, int n, kron_dtype io, kron_c
         return KRON_ERR_INVALID_VALUE;
     std::lock_guard<std::mutex> lock(g_mu);
     load_cache_locked();
-    if (instances_per_tile == 0 && pipeline_depth == 0)
-        g_table.erase(Key(kind, n, (int)io, (int)comp));
-    else
-        g_table[Key(kind, n, (int)io, (int)comp)] = Entry{instances_per_tile, pipeline_depth, 0, 0};
+    put_locked(Key(kind, n, (int)io, (int)comp), Entry{instances_per_tile, pipeline_depth, 0, 0, 0});
     return KRON_OK;
 }
 
@@ -208,7 +232,7 @@ KRON_API kron_status kron_autotune_config(kron_stream_t stream, int kind, int n,
     // fiber per thread" (the in-place bodies: their own tile shapes), pipeline
     // depths 1 and 2, and for the packed-pair bodies one or two fibers per step.
     std::vector<kron_kernel_config> cands;
-    cands.push_back(kron_kernel_config{0, 0, 0, 0});
+    cands.push_back(kron_kernel_config{0, 0, 0, 0, 0});
     const int base = kind == 2 ? (256 + n - 1) / n : (256 + n * n - 1) / (n * n);
     for (int var = KRON_VARIANT_IN_PLACE; var <= KRON_VARIANT_SCALAR; ++var) {
         if (!variant_ok(kind, n, io, comp, var, 0) && var != KRON_VARIANT_IN_PLACE) continue;
@@ -224,27 +248,31 @@ KRON_API kron_status kron_autotune_config(kron_stream_t stream, int kind, int n,
             for (int ns : {1, 2})
                 for (int fps : {1, 2}) {
                     if (fps == 2 && var != KRON_VARIANT_EXCHANGE) continue;
-                    cands.push_back(kron_kernel_config{var, P, ns, var == KRON_VARIANT_EXCHANGE ? fps : 0});
+                    cands.push_back(kron_kernel_config{var, P, ns, var == KRON_VARIANT_EXCHANGE ? fps : 0, 0});
                 }
+    }
+    if (kind == 2 && n == 16 && io == KRON_R32F && comp == KRON_COMPUTE_NATIVE) {
+        // The tensor-copy in-place body: tile, ring depth and compute warps
+        // (registers against shared memory: a deeper ring leaves room for
+        // fewer resident warps).
+        const int shapes[][3] = {{32, 5, 16}, {32, 4, 16}, {32, 3, 8}, {16, 8, 16}, {16, 6, 12},
+                                 {16, 4, 8},  {24, 3, 12}, {24, 6, 12}, {8, 8, 8}};
+        for (const auto& s : shapes) cands.push_back(kron_kernel_config{KRON_VARIANT_IN_PLACE, s[0], s[1], 0, s[2]});
     }
     if (comp != KRON_COMPUTE_NATIVE || !real_io(io)) {   // one body: tile and depth only
         cands.resize(1);
         for (int mul2 : {1, 2, 4, 8})
-            for (int ns : {1, 2}) cands.push_back(kron_kernel_config{0, std::max(1, base * mul2 / 2), ns, 0});
+            for (int ns : {1, 2}) cands.push_back(kron_kernel_config{0, std::max(1, base * mul2 / 2), ns, 0, 0});
     }
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return KRON_ERR_CUDA;
     float best = 1e30f, t_default = 1e30f;
-    kron_kernel_config best_c{0, 0, 0, 0};
+    kron_kernel_config best_c{0, 0, 0, 0, 0};
     kron_status rs = KRON_OK;
     for (const kron_kernel_config& c : cands) {
         {
             std::lock_guard<std::mutex> lock(g_mu);
-            if (c.variant == 0 && c.instances_per_tile == 0 && c.pipeline_depth == 0 && c.fibers_per_step == 0)
-                g_table.erase(Key(kind, n, (int)io, (int)comp));
-            else
-                g_table[Key(kind, n, (int)io, (int)comp)] =
-                    Entry{c.instances_per_tile, c.pipeline_depth, c.variant, c.fibers_per_step};
+            put_locked(Key(kind, n, (int)io, (int)comp), entry_of(c));
         }
         if (run() != KRON_OK) continue;   // not available at this size (e.g. shared memory)
         float t = 1e30f;
@@ -258,7 +286,7 @@ KRON_API kron_status kron_autotune_config(kron_stream_t stream, int kind, int n,
             t = std::min(t, ms);
         }
         if (rs != KRON_OK) break;
-        if (c.variant == 0 && c.instances_per_tile == 0 && c.pipeline_depth == 0) t_default = t;
+        if (is_default(entry_of(c))) t_default = t;
         if (t < best) { best = t; best_c = c; }
     }
     cudaEventDestroy(e0);
@@ -267,14 +295,11 @@ KRON_API kron_status kron_autotune_config(kron_stream_t stream, int kind, int n,
         kron_set_kernel_config(kind, n, io, comp, &prev);
         return rs;
     }
-    if (best > 0.98f * t_default) best_c = kron_kernel_config{0, 0, 0, 0};   // not clearly better: keep the default
+    if (best > 0.98f * t_default) best_c = kron_kernel_config{0, 0, 0, 0, 0};   // not clearly better: keep the default
     {
         std::lock_guard<std::mutex> lock(g_mu);
-        const Entry e{best_c.instances_per_tile, best_c.pipeline_depth, best_c.variant, best_c.fibers_per_step};
-        if (e.P == 0 && e.nstage == 0 && e.variant == 0 && e.fps == 0)
-            g_table.erase(Key(kind, n, (int)io, (int)comp));
-        else
-            g_table[Key(kind, n, (int)io, (int)comp)] = e;
+        const Entry e = entry_of(best_c);
+        put_locked(Key(kind, n, (int)io, (int)comp), e);
         append_cache(Key(kind, n, (int)io, (int)comp), e);   // all zero records "default kept"
     }
     if (out) *out = best_c;

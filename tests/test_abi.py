@@ -203,7 +203,9 @@ def test_kernel_config_validation_and_round_trip(lib):
     f32 = kg.DTYPES["f32"]
     # out of range
     assert lib.kron_set_kernel_config(2, 16, f32, 0, ctypes.byref(cfg(9, 0, 0, 0))) == INVALID
-    assert lib.kron_set_kernel_config(2, 16, f32, 0, ctypes.byref(cfg(2, 0, 9, 0))) == INVALID
+    assert lib.kron_set_kernel_config(2, 16, f32, 0, ctypes.byref(cfg(2, 0, 13, 0))) == INVALID
+    assert lib.kron_set_kernel_config(2, 16, f32, 0, ctypes.byref(cfg(1, 32, 5, 0, 17))) == INVALID
+    assert lib.kron_set_kernel_config(2, 16, f32, 0, ctypes.byref(cfg(1, 32, 5, 0, -1))) == INVALID
     assert lib.kron_set_kernel_config(2, 16, f32, 0, ctypes.byref(cfg(2, 0, 0, 3))) == INVALID
     assert lib.kron_set_kernel_config(2, 17, f32, 0, ctypes.byref(cfg(0, 0, 0, 0))) == INVALID
     assert lib.kron_set_kernel_config(2, 16, f32, 0, None) == INVALID
@@ -212,7 +214,18 @@ def test_kernel_config_validation_and_round_trip(lib):
     assert lib.kron_set_kernel_config(2, 7, f32, 0, ctypes.byref(cfg(2, 0, 0, 0))) == NOTSUP_    # pairs need even n
     assert lib.kron_set_kernel_config(2, 16, kg.DTYPES["f64"], 0, ctypes.byref(cfg(2, 0, 0, 0))) == NOTSUP_
     assert lib.kron_set_kernel_config(2, 16, f32, 1, ctypes.byref(cfg(3, 0, 0, 0))) == NOTSUP_   # tensor path: one body
-    assert lib.kron_set_kernel_config(2, 16, f32, 0, ctypes.byref(cfg(1, 7, 0, 0))) == NOTSUP_   # in place takes 16
+    assert lib.kron_set_kernel_config(2, 16, f32, 0, ctypes.byref(cfg(1, 7, 0, 0))) == NOTSUP_   # in place: 8..32 by 8
+    assert lib.kron_set_kernel_config(2, 16, kg.DTYPES["bf16"], 0, ctypes.byref(cfg(1, 32, 0, 0))) == NOTSUP_
+    # compute warps: only the FP32 2-D n = 16 in-place body, in groups of P / 4
+    assert lib.kron_set_kernel_config(2, 16, f32, 0, ctypes.byref(cfg(1, 32, 5, 0, 12))) == NOTSUP_
+    assert lib.kron_set_kernel_config(2, 16, f32, 0, ctypes.byref(cfg(2, 0, 2, 0, 8))) == NOTSUP_
+    assert lib.kron_set_kernel_config(2, 12, f32, 0, ctypes.byref(cfg(0, 0, 0, 0, 8))) == NOTSUP_
+    assert lib.kron_set_kernel_config(2, 16, kg.DTYPES["bf16"], 0, ctypes.byref(cfg(1, 16, 0, 0, 4))) == NOTSUP_
+    assert lib.kron_set_kernel_config(2, 16, f32, 0, ctypes.byref(cfg(1, 24, 3, 0, 12))) == 0
+    got = cfg()
+    assert lib.kron_get_kernel_config(2, 16, f32, 0, ctypes.byref(got)) == 0
+    assert (got.variant, got.instances_per_tile, got.pipeline_depth, got.compute_warps) == (1, 24, 3, 12)
+    assert lib.kron_set_kernel_config(2, 16, f32, 0, ctypes.byref(cfg())) == 0
     # round trip, then back to the default
     assert lib.kron_set_kernel_config(3, 12, f32, 0, ctypes.byref(cfg(2, 6, 2, 2))) == 0
     got = cfg()

@@ -4,6 +4,7 @@ leaves a configuration that does too."""
 import numpy as np
 import pytest
 
+import oracle
 import paper_1304_7054_gb300 as kg
 from paper_1304_7054_gb300 import inputs
 
@@ -76,6 +77,36 @@ def test_kernel_configs_give_the_same_result(kind, n, io, variant, P, depth, fps
     finally:
         kg.set_kernel_config(kind, n, io)
     check(Y, b, X64, io)
+
+
+# The FP32 2-D n = 16 in-place body (tiles moved by tensor copies): tiles,
+# ring depths and compute-warp groups, on a batch whose last tile is partial,
+# with alpha and beta.
+@pytest.mark.parametrize("P,depth,warps", [(8, 8, 8), (16, 8, 16), (24, 3, 12), (32, 5, 16), (32, 2, 8), (16, 2, 4),
+                                           (8, 1, 2), (32, 12, 16)])
+@pytest.mark.parametrize("batch", [1, 7, 1003])
+def test_tensor_copy_body_configs(P, depth, warps, batch):
+    import torch
+    b = inputs.make_batch(2, 16, batch, seed=580 + P + batch, x_dist="normal")
+    kg.set_kernel_config(2, 16, "f32", "native", "in_place", P, depth, 0, warps)
+    try:
+        assert kg.get_kernel_config(2, 16, "f32")["compute_warps"] == warps
+        Y, X64 = run_gpu(b, io="f32", guard=8)
+        check(Y, b, X64, "f32")
+        # beta != 0 reads Y for the live instances of the last tile only
+        rng = np.random.default_rng(batch)
+        Y0 = rng.standard_normal(batch * 256).astype(np.float32)
+        Yd = torch.from_numpy(Y0.copy()).cuda()
+        X = torch.from_numpy(b.X).cuda()
+        kg.kron2_batched(b.A, b.B, X, Yd, ma=16, na=16, mb=16, nb=16, batch=batch, alpha=0.5, beta=-2.0)
+        torch.cuda.synchronize()
+        assert kg.device_status() == 0
+        R = oracle.kron2(b.A.astype(np.float64), b.B.astype(np.float64), b.X.astype(np.float64), ma=16, na=16, mb=16,
+                         nb=16, batch=batch, alpha=0.5, beta=-2.0, Y=Y0.astype(np.float64))
+        scale = np.abs(R).max() + 1.0
+        assert np.abs(Yd.cpu().numpy().astype(np.float64) - R).max() <= 1e-5 * scale * 16
+    finally:
+        kg.set_kernel_config(2, 16, "f32")
 
 
 @pytest.mark.parametrize("kind,n,io", [(3, 16, "f32"), (2, 12, "bf16"), (3, 9, "f32")])
