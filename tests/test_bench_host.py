@@ -22,7 +22,7 @@ def test_reference_arm_json_line():
 def test_kernel_names_follow_dispatch():
     sys.path.insert(0, ROOT)
     import bench
-    assert bench.kernel_of(2, 16, "f32", "native").startswith("pair16_kernel")
+    assert bench.kernel_of(2, 16, "f32", "native").startswith("pair16t_kernel")
     assert bench.kernel_of(2, 16, "bf16", "native").startswith("pair16h_kernel")
     assert bench.kernel_of(2, 10, "f32", "native").startswith("pair2ip_kernel")
     assert bench.kernel_of(2, 12, "f32", "native").startswith("pair_kernel")
