@@ -739,7 +739,7 @@ def run_ours(args):
         for name, r in variants.items():
             w = WORKLOADS.get(name)
             if w and "gflops" in r and w["compute"] == "native":
-                unit = {"f64": "dfma", "c128": "dfma", "c64": "ffma"}.get(w["io"], "ffma2")
+                unit = {"f64": "dfma", "c128": "dfma"}.get(w["io"], "ffma2")
                 r["of_measured_fma_peak"] = round(r["gflops"] / (alu[unit]["tflops"] * 1e3), 4)
         cpu = cpu_baseline(b, seconds=args.cpu_seconds)
         out = {
