@@ -295,14 +295,19 @@ KRON_API kron_status kron_autotune(kron_stream_t stream, int kind, int n, int64_
  *   fibers_per_step:    register blocking of the last contraction of the
  *                       packed-pair bodies: 1 or 2 fibers per thread and step
  *                       (0 = default)
- *   compute_warps:      compute warps per CTA (0 = default).  Only the FP32
- *                       2-D n = 16 in-place body takes it: its warps work in
- *                       groups of instances_per_tile / 4, each group on its
- *                       own tile of the ring, so compute_warps must be a
- *                       multiple of that, at most 16.  With pipeline_depth
- *                       (up to 12 tiles for that body, 8 for the others) it
- *                       sets the split of an SM between registers (resident
- *                       warps) and shared memory (tiles in flight).
+ *   compute_warps:      compute warps per CTA (0 = default).  Two bodies
+ *                       take it.  The FP32 2-D n = 16 in-place body: its
+ *                       warps work in groups of instances_per_tile / 4, each
+ *                       group on its own tile of the ring, so compute_warps
+ *                       must be a multiple of that, at most 16; with
+ *                       pipeline_depth (up to 12 tiles for that body, 8 for
+ *                       the others) it sets the split of an SM between
+ *                       registers (resident warps) and shared memory (tiles
+ *                       in flight).  The 3-D split tensor body
+ *                       (KRON_COMPUTE_32F_BF16X3): 1 = one warp per instance
+ *                       and CTA; 2, 4 or 8 = that many warps share one
+ *                       instance (a CTA barrier between the modes) with the
+ *                       next instance's operand arriving meanwhile.
  *
  * kron_set_kernel_config returns KRON_ERR_NOT_SUPPORTED when the body does not
  * exist for (kind, n, io, comp) (in place: 2-D n = 16 any storage -- FP32 with
@@ -312,7 +317,8 @@ KRON_API kron_status kron_autotune(kron_stream_t stream, int kind, int n, int64_
  * values out of range; all-zero restores the built-in default.  Strided,
  * transposed or misaligned batches always run the scalar body.  The split
  * tensor path (KRON_COMPUTE_32F_BF16X3) and complex storage have one body each:
- * only instances_per_tile and pipeline_depth apply there.
+ * only instances_per_tile and pipeline_depth apply there (and compute_warps
+ * for the 3-D tensor body).
  *
  * kron_autotune_config times every configuration of that space on the
  * caller's buffers (as kron_autotune; Y is overwritten), keeps the fastest

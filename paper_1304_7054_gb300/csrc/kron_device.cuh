@@ -29,6 +29,19 @@ __device__ __forceinline__ f2 fmul2(f2 a, f2 b) {
     return d;
 }
 
+// A float pair rounded (RNE) to two packed 16-bit storage values.
+template <typename S> __device__ __forceinline__ unsigned pack16(f2 v);
+template <> __device__ __forceinline__ unsigned pack16<__nv_bfloat16>(f2 v) {
+    unsigned r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(f2_hi(v)), "f"(f2_lo(v)));
+    return r;
+}
+template <> __device__ __forceinline__ unsigned pack16<__half>(f2 v) {
+    unsigned r;
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(f2_hi(v)), "f"(f2_lo(v)));
+    return r;
+}
+
 // Bits of the device status word (see kron_device_status in kron.h).
 constexpr unsigned kDevErrTimeout = 1u;
 // A bounded wait gives up after this many nanoseconds of %globaltimer.

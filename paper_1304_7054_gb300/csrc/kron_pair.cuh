@@ -39,18 +39,6 @@ template <> __device__ __forceinline__ f2 load_pair<__half>(const __half* p) {
     return f2_pack(v.x, v.y);
 }
 
-// A float pair rounded (RNE) to two packed 16-bit storage values.
-template <typename S> __device__ __forceinline__ unsigned pack16(f2 v);
-template <> __device__ __forceinline__ unsigned pack16<__nv_bfloat16>(f2 v) {
-    unsigned r;
-    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(f2_hi(v)), "f"(f2_lo(v)));
-    return r;
-}
-template <> __device__ __forceinline__ unsigned pack16<__half>(f2 v) {
-    unsigned r;
-    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(f2_hi(v)), "f"(f2_lo(v)));
-    return r;
-}
 
 // y[k] = Md[k, :] . x for the two fibers packed in x (Md: duplicated coefficients).
 template <int N>

@@ -21,6 +21,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <type_traits>
 
 #include "kron_device.cuh"
@@ -32,6 +33,15 @@ namespace kron {
 __device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
     asm volatile(
         "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// The same shape on f16 operands (f16 storage: the stored operand enters as it is).
+__device__ __forceinline__ void mma_f16_16816(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
         "{%0,%1,%2,%3};"
         : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
@@ -51,6 +61,11 @@ struct TcArgs2 {
     // word r*8 + c/2 holds (M[r][c], M[r][c+1]); hi and lo parts of the split.
     unsigned m1h[128], m1l[128];
     unsigned m2h[128], m2l[128];
+    // f16 storage: M1 * 2^s as an f16 split (the first product then takes the
+    // stored f16 operand as it is, two MMAs instead of three); M2 above is then
+    // scaled by 2^-s.  f16a = 0: not used (bf16 split of the operand instead).
+    unsigned f1h[128], f1l[128];
+    int f16a;
     const void* X;
     void* Y;
     int64_t batch;
@@ -68,13 +83,15 @@ __device__ __forceinline__ void x_pair(const S* xq, int l, int m, float& v0, flo
     v1 = (l + 1 < N && m < N) ? load_cvt<float, S>(xq[l + 1 + N * m]) : 0.f;
 }
 
-template <int N>
-__device__ __forceinline__ unsigned x_pair_bf16(const __nv_bfloat16* xq, int l, int m) {
+// The same pair of a 16-bit operand as its raw bits (two packed values).
+template <int N, typename S>
+__device__ __forceinline__ unsigned x_pair_bf16(const S* xq, int l, int m) {
+    const unsigned short* xs = reinterpret_cast<const unsigned short*>(xq);
     if constexpr (N % 2 == 0) {
-        return (l < N && m < N) ? *reinterpret_cast<const unsigned*>(xq + l + N * m) : 0u;
+        return (l < N && m < N) ? *reinterpret_cast<const unsigned*>(xs + l + N * m) : 0u;
     } else {
-        const unsigned a = (l < N && m < N) ? (unsigned)__bfloat16_as_ushort(xq[l + N * m]) : 0u;
-        const unsigned b = (l + 1 < N && m < N) ? (unsigned)__bfloat16_as_ushort(xq[l + 1 + N * m]) : 0u;
+        const unsigned a = (l < N && m < N) ? (unsigned)xs[l + N * m] : 0u;
+        const unsigned b = (l + 1 < N && m < N) ? (unsigned)xs[l + 1 + N * m] : 0u;
         return a | (b << 16);
     }
 }
@@ -97,8 +114,8 @@ __device__ __forceinline__ void x_pair_blk(const S* const (&xq)[16 / B], int l, 
     }
 }
 
-template <int N, int B>
-__device__ __forceinline__ unsigned x_pair_bf16_blk(const __nv_bfloat16* const (&xq)[16 / B], int l, int m) {
+template <int N, int B, typename S>
+__device__ __forceinline__ unsigned x_pair_bf16_blk(const S* const (&xq)[16 / B], int l, int m) {
     const int b = l / B;
     return (b == m / B && xq[b]) ? x_pair_bf16<N>(xq[b], l % B, m % B) : 0u;
 }
@@ -108,7 +125,8 @@ template <typename S, int N, int B>
 __device__ __forceinline__ void tc2_instance(const TcArgs2<N>& a, const S* const (&xq)[16 / B],
                                              S* const (&yq)[16 / B], const unsigned (&m1h)[4],
                                              const unsigned (&m1l)[4], const unsigned (&m2h)[2][2],
-                                             const unsigned (&m2l)[2][2]) {
+                                             const unsigned (&m2l)[2][2], const unsigned (&f1h)[4],
+                                             const unsigned (&f1l)[4]) {
     const int lane = threadIdx.x & 31;
     const int g = lane >> 2, t = lane & 3;
     // ---- stage 1: W = M1 X ---------------------------------------------------------------
@@ -123,6 +141,11 @@ __device__ __forceinline__ void tc2_instance(const TcArgs2<N>& a, const S* const
             const unsigned b1 = x_pair_bf16_blk<N, B>(xq, 2 * t + 8, m);
             mma_bf16_16816(w[nt], m1l, b0, b1);
             mma_bf16_16816(w[nt], m1h, b0, b1);
+        } else if (std::is_same<S, __half>::value && a.f16a) {
+            const unsigned b0 = x_pair_bf16_blk<N, B>(xq, 2 * t, m);
+            const unsigned b1 = x_pair_bf16_blk<N, B>(xq, 2 * t + 8, m);
+            mma_f16_16816(w[nt], f1l, b0, b1);
+            mma_f16_16816(w[nt], f1h, b0, b1);
         } else {
             float x0, x1, x2, x3;
             if constexpr (N == 16 && sizeof(S) == 4) {
@@ -188,7 +211,13 @@ __global__ void __launch_bounds__(kTcThreads) tc2_kernel(const __grid_constant__
 
     // Constant fragments: A of M1 (rows g, g+8; pair columns t, t+4) and B of
     // M2^T for both n-tiles (column j = 8 nt + g of M2^T is row j of M2).
-    unsigned m1h[4], m1l[4], m2h[2][2], m2l[2][2];
+    unsigned m1h[4], m1l[4], m2h[2][2], m2l[2][2], f1h[4] = {0u, 0u, 0u, 0u}, f1l[4] = {0u, 0u, 0u, 0u};
+    if (std::is_same<S, __half>::value && a.f16a) {
+        f1h[0] = a.f1h[g * 8 + t];           f1l[0] = a.f1l[g * 8 + t];
+        f1h[1] = a.f1h[(g + 8) * 8 + t];     f1l[1] = a.f1l[(g + 8) * 8 + t];
+        f1h[2] = a.f1h[g * 8 + t + 4];       f1l[2] = a.f1l[g * 8 + t + 4];
+        f1h[3] = a.f1h[(g + 8) * 8 + t + 4]; f1l[3] = a.f1l[(g + 8) * 8 + t + 4];
+    }
     m1h[0] = a.m1h[g * 8 + t];       m1l[0] = a.m1l[g * 8 + t];
     m1h[1] = a.m1h[(g + 8) * 8 + t]; m1l[1] = a.m1l[(g + 8) * 8 + t];
     m1h[2] = a.m1h[g * 8 + t + 4];   m1l[2] = a.m1l[g * 8 + t + 4];
@@ -244,7 +273,7 @@ __global__ void __launch_bounds__(kTcThreads) tc2_kernel(const __grid_constant__
                     xq[b] = live ? xt + (q0 + b) * NX : nullptr;
                     yq[b] = live ? static_cast<S*>(a.Y) + (inst0 + q0 + b) * NX : nullptr;
                 }
-                tc2_instance<S, N, B>(a, xq, yq, m1h, m1l, m2h, m2l);
+                tc2_instance<S, N, B>(a, xq, yq, m1h, m1l, m2h, m2l, f1h, f1l);
             }
         }
         if (__syncthreads_or(!ok)) {
@@ -295,10 +324,13 @@ struct TcArgs3 {
     unsigned m1h[128], m1l[128];   // row-major packed bf16 pairs, as TcArgs2
     unsigned m2h[128], m2l[128];
     unsigned m3h[128], m3l[128];
+    unsigned f2h[128], f2l[128];   // f16 storage: M2 * 2^s as an f16 split (M1 scaled by 2^-s)
+    int f16a;                      // 0: not used
     const void* X;
     void* Y;
     int64_t batch;
     int beta_zero, alpha_one;
+    int ypair;                     // Y 4-byte aligned: 16-bit results leave as pairs
     float alpha, beta;
     unsigned* err;
 };
@@ -341,9 +373,50 @@ __device__ __forceinline__ float xval(const S* xs, int l, int m, int p) {
 }
 
 // Modes 1 and 2 of plane p: writes row p of T (hi and lo halves).
+// f16a (f16 storage): bh receives the raw f16 pairs, for f16 MMAs.
 template <typename S, int N>
 __device__ __forceinline__ void tc3_plane_load(const S* xs, int p, int g, int t, unsigned (&bh)[4],
-                                               unsigned (&bl)[4]) {
+                                               unsigned (&bl)[4], bool f16a) {
+    if constexpr (N == 16 && sizeof(S) == 2) {
+        // 16-bit planes: the four 8 x 8 blocks of X_p^T by one ldmatrix.trans.
+        // Matrix mi = 2 nt + h holds rows m = 8 h + r (16 contiguous bytes: l =
+        // 8 nt .. 8 nt + 7), so lane (g, t) receives X_p[8 nt + g][8 h + 2t, +1].
+        const int lane = 4 * g + t, mi = lane >> 3, r = lane & 7;
+        unsigned v[4];
+        ldsm_x4_trans(v, smem_u32(xs + 8 * (mi >> 1) + 16 * (8 * (mi & 1) + r) + 256 * p));
+        if constexpr (std::is_same<S, __nv_bfloat16>::value) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                bh[e] = v[e];   // bfloat16 operands are their own hi part
+                bl[e] = 0u;
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                if (f16a) {
+                    bh[e] = v[e];
+                    bl[e] = 0u;
+                } else {
+                    const float2 x = __half22float2(*reinterpret_cast<const __half2*>(&v[e]));
+                    split_pair(x.x, x.y, bh[e], bl[e]);
+                }
+            }
+        }
+        return;
+    }
+    if (std::is_same<S, __half>::value && f16a) {
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+            const int l = 8 * nt + g;
+            // B pairs run along m (stride N in the plane): two raw 16-bit values each
+            const unsigned short* xp = reinterpret_cast<const unsigned short*>(xs) + N * N * p;
+            auto raw = [&](int ll, int m) -> unsigned { return (ll < N && m < N) ? (unsigned)xp[ll + N * m] : 0u; };
+            bh[2 * nt] = raw(l, 2 * t) | (raw(l, 2 * t + 1) << 16);
+            bh[2 * nt + 1] = raw(l, 2 * t + 8) | (raw(l, 2 * t + 9) << 16);
+            bl[2 * nt] = bl[2 * nt + 1] = 0u;
+        }
+        return;
+    }
     // B fragment of X_p^T for n-tiles nt = 0, 1: column n = l = 8 nt + g,
     // rows k = m = 2t, 2t+1 and 2t+8, 2t+9
 #pragma unroll
@@ -357,16 +430,24 @@ __device__ __forceinline__ void tc3_plane_load(const S* xs, int p, int g, int t,
 
 // XEXACT: the operand is a bfloat16 value (bf16 storage), so its lo part is zero
 // and the product with it is skipped.
+// f16a: the operand pairs are raw f16 values and the first product runs as f16
+// MMAs with the f16 split of M2 (f2h, f2l).
 template <bool XEXACT>
 __device__ __forceinline__ void tc3_plane_compute(const unsigned (&bh)[4], const unsigned (&bl)[4],
                                                   const unsigned (&m2h)[4], const unsigned (&m2l)[4],
                                                   const unsigned (&m1h)[2][2], const unsigned (&m1l)[2][2],
-                                                  float (&z)[2][4]) {
+                                                  float (&z)[2][4], bool f16a, const unsigned (&f2h)[4],
+                                                  const unsigned (&f2l)[4]) {
     float w[2][4];
 #pragma unroll
     for (int nt = 0; nt < 2; ++nt) {
 #pragma unroll
         for (int e = 0; e < 4; ++e) w[nt][e] = 0.f;
+        if (f16a) {
+            mma_f16_16816(w[nt], f2l, bh[2 * nt], bh[2 * nt + 1]);
+            mma_f16_16816(w[nt], f2h, bh[2 * nt], bh[2 * nt + 1]);
+            continue;
+        }
         mma_bf16_16816(w[nt], m2l, bh[2 * nt], bh[2 * nt + 1]);
         if constexpr (!XEXACT) mma_bf16_16816(w[nt], m2h, bl[2 * nt], bl[2 * nt + 1]);
         mma_bf16_16816(w[nt], m2h, bh[2 * nt], bh[2 * nt + 1]);
@@ -416,6 +497,24 @@ __device__ __forceinline__ void tc3_rows(const TcArgs3<N>& a, S* yq, uint32_t tb
         mma_bf16_16816(y, al, m3h[nt][0], m3h[nt][1]);
         mma_bf16_16816(y, ah, m3l[nt][0], m3l[nt][1]);
         mma_bf16_16816(y, ah, m3h[nt][0], m3h[nt][1]);
+        if constexpr (N == 16 && sizeof(S) == 2) {
+            if (a.beta_zero && a.ypair) {
+                // Pairs of adjacent rows i (lanes g, g ^ 1) as one 32-bit store:
+                // the even lane stores column k = 2t, the odd lane k = 2t + 1.
+                float v[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) v[e] = a.alpha_one ? y[e] : a.alpha * y[e];
+                const bool odd = g & 1;
+                const float s1 = __shfl_xor_sync(0xffffffffu, odd ? v[0] : v[1], 4);
+                const float s3 = __shfl_xor_sync(0xffffffffu, odd ? v[2] : v[3], 4);
+                const int i0 = g & ~1, k = 8 * nt + 2 * t + (odd ? 1 : 0);
+                const f2 lo = odd ? f2_pack(s1, v[1]) : f2_pack(v[0], s1);
+                const f2 hi = odd ? f2_pack(s3, v[3]) : f2_pack(v[2], s3);
+                *reinterpret_cast<unsigned*>(yq + i0 + N * mt + N * N * k) = pack16<S>(lo);
+                *reinterpret_cast<unsigned*>(yq + i0 + 8 + N * mt + N * N * k) = pack16<S>(hi);
+                continue;
+            }
+        }
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const int i = g + 8 * (e >> 1), k = 8 * nt + 2 * t + (e & 1);
@@ -450,6 +549,14 @@ __global__ void __launch_bounds__(32 * kTc3Warps) tc3_kernel(const __grid_consta
     // Constant fragments.  A of M2 (rows j', columns m); B of M1^T and M3^T:
     // column n of M^T is row n of M, pairs along the row.
     unsigned m2h[4], m2l[4], m1h[2][2], m1l[2][2], m3h[2][2], m3l[2][2];
+    const bool f16a = std::is_same<S, __half>::value && a.f16a;
+    unsigned f2h[4] = {0u, 0u, 0u, 0u}, f2l[4] = {0u, 0u, 0u, 0u};
+    if (f16a) {
+        f2h[0] = a.f2h[g * 8 + t];           f2l[0] = a.f2l[g * 8 + t];
+        f2h[1] = a.f2h[(g + 8) * 8 + t];     f2l[1] = a.f2l[(g + 8) * 8 + t];
+        f2h[2] = a.f2h[g * 8 + t + 4];       f2l[2] = a.f2l[g * 8 + t + 4];
+        f2h[3] = a.f2h[(g + 8) * 8 + t + 4]; f2l[3] = a.f2l[(g + 8) * 8 + t + 4];
+    }
     m2h[0] = a.m2h[g * 8 + t];           m2l[0] = a.m2l[g * 8 + t];
     m2h[1] = a.m2h[(g + 8) * 8 + t];     m2l[1] = a.m2l[(g + 8) * 8 + t];
     m2h[2] = a.m2h[g * 8 + t + 4];       m2l[2] = a.m2l[g * 8 + t + 4];
@@ -500,11 +607,11 @@ __global__ void __launch_bounds__(32 * kTc3Warps) tc3_kernel(const __grid_consta
         for (int p = 0; p < N; p += 2) {
             const bool two = p + 1 < N;
             unsigned bh0[4], bl0[4], bh1[4], bl1[4];
-            tc3_plane_load<S, N>(xq, p, g, t, bh0, bl0);
-            if (two) tc3_plane_load<S, N>(xq, p + 1, g, t, bh1, bl1);
+            tc3_plane_load<S, N>(xq, p, g, t, bh0, bl0, f16a);
+            if (two) tc3_plane_load<S, N>(xq, p + 1, g, t, bh1, bl1, f16a);
             float z0[2][4], z1[2][4];
-            tc3_plane_compute<XEXACT>(bh0, bl0, m2h, m2l, m1h, m1l, z0);
-            if (two) tc3_plane_compute<XEXACT>(bh1, bl1, m2h, m2l, m1h, m1l, z1);
+            tc3_plane_compute<XEXACT>(bh0, bl0, m2h, m2l, m1h, m1l, z0, f16a, f2h, f2l);
+            if (two) tc3_plane_compute<XEXACT>(bh1, bl1, m2h, m2l, m1h, m1l, z1, f16a, f2h, f2l);
             __syncwarp();   // planes p, p+1 are read by every lane before they are overwritten
             tc3_plane_store(tb, p, g, t, z0);
             if (two) tc3_plane_store(tb, p + 1, g, t, z1);
@@ -533,6 +640,121 @@ __global__ void __launch_bounds__(32 * kTc3Warps) tc3_kernel(const __grid_consta
     }
 }
 
+// 3-D, several warps per instance (tc3g_kernel): the CTA's W warps share one
+// instance -- modes 1 and 2 split by plane pairs, mode 3 by row-block pairs,
+// a CTA barrier between the two -- and the operand buffer is doubled, so the
+// next instance lands while this one is contracted.  Per CTA: two operand
+// buffers and (except FP32 n = 16, where T overwrites the operand planes) one
+// T buffer: 32 KB at n = 16 against 16-24 KB per single-warp CTA, for 4-8
+// times the warps per instance.
+template <typename S, int N>
+__global__ void __launch_bounds__(256) tc3g_kernel(const __grid_constant__ TcArgs3<N> a) {
+    using L = Tc3Layout<S, N>;
+    constexpr int NX = N * N * N;
+    constexpr unsigned NXB = NX * (unsigned)sizeof(S);
+    constexpr bool XEXACT = std::is_same<S, __nv_bfloat16>::value;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int W = blockDim.x >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, t = lane & 3;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem);   // one barrier per operand buffer
+    unsigned char* xbuf = smem + 128;                     // operand buffers, L::XB bytes each
+    unsigned char* tsep = xbuf + 2 * L::XB;               // T, unless in place
+
+    unsigned m2h[4], m2l[4], m1h[2][2], m1l[2][2], m3h[2][2], m3l[2][2];
+    const bool f16a = std::is_same<S, __half>::value && a.f16a;
+    unsigned f2h[4] = {0u, 0u, 0u, 0u}, f2l[4] = {0u, 0u, 0u, 0u};
+    if (f16a) {
+        f2h[0] = a.f2h[g * 8 + t];           f2l[0] = a.f2l[g * 8 + t];
+        f2h[1] = a.f2h[(g + 8) * 8 + t];     f2l[1] = a.f2l[(g + 8) * 8 + t];
+        f2h[2] = a.f2h[g * 8 + t + 4];       f2l[2] = a.f2l[g * 8 + t + 4];
+        f2h[3] = a.f2h[(g + 8) * 8 + t + 4]; f2l[3] = a.f2l[(g + 8) * 8 + t + 4];
+    }
+    m2h[0] = a.m2h[g * 8 + t];           m2l[0] = a.m2l[g * 8 + t];
+    m2h[1] = a.m2h[(g + 8) * 8 + t];     m2l[1] = a.m2l[(g + 8) * 8 + t];
+    m2h[2] = a.m2h[g * 8 + t + 4];       m2l[2] = a.m2l[g * 8 + t + 4];
+    m2h[3] = a.m2h[(g + 8) * 8 + t + 4]; m2l[3] = a.m2l[(g + 8) * 8 + t + 4];
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) {
+        const int n = 8 * nt + g;
+        m1h[nt][0] = a.m1h[n * 8 + t];     m1l[nt][0] = a.m1l[n * 8 + t];
+        m1h[nt][1] = a.m1h[n * 8 + t + 4]; m1l[nt][1] = a.m1l[n * 8 + t + 4];
+        m3h[nt][0] = a.m3h[n * 8 + t];     m3l[nt][0] = a.m3l[n * 8 + t];
+        m3h[nt][1] = a.m3h[n * 8 + t + 4]; m3l[nt][1] = a.m3l[n * 8 + t + 4];
+    }
+    if constexpr (!L::INPLACE) {
+        for (int e = threadIdx.x; e < (16 - N) * 256; e += blockDim.x)
+            reinterpret_cast<unsigned*>(tsep + N * 1024)[e] = 0u;
+    }
+
+    const int64_t G = gridDim.x;
+    int64_t inst = blockIdx.x;
+    uint64_t pol = 0;
+    auto phase = [&](int64_t q) -> int {
+        if constexpr (L::ALIGNED) return 0;
+        else return (int)(((uintptr_t)(static_cast<const S*>(a.X) + q * NX) & 15u) / sizeof(S));
+    };
+    auto fetch = [&](int b, int64_t q) {
+        const int ph = phase(q);
+        const unsigned bytes = (unsigned)(ph * sizeof(S) + NXB + 15u) & ~15u;
+        mbar_arrive_expect_tx(&full[b], bytes);
+        bulk_g2s(xbuf + b * L::XB, static_cast<const S*>(a.X) + q * NX - ph, bytes, &full[b], pol);
+    };
+    if (threadIdx.x == 0) {
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        fence_barrier_init();
+        pol = l2_evict_first_policy();
+        if (inst < a.batch) fetch(0, inst);
+        if (inst + G < a.batch) fetch(1, inst + G);
+    }
+    __syncthreads();
+    for (int it = 0; inst < a.batch; inst += G, ++it) {
+        const int b = it & 1;
+        const bool ok = mbar_wait_bounded(&full[b], (unsigned)(it >> 1) & 1u, a.err);
+        if (__syncthreads_or(!ok)) {
+            // wait (bounded) for the copies that may still be in flight, then give up
+            if (threadIdx.x == 0) {
+                mbar_wait_bounded(&full[b], (unsigned)(it >> 1) & 1u, a.err);
+                if (inst + G < a.batch) mbar_wait_bounded(&full[b ^ 1], (unsigned)((it + 1) >> 1) & 1u, a.err);
+            }
+            return;
+        }
+        const S* xq = reinterpret_cast<const S*>(xbuf + b * L::XB) + phase(inst);
+        unsigned char* tb = L::INPLACE ? xbuf + b * L::XB : tsep;
+        const uint32_t tb_s = smem_u32(tb);
+
+        // ---- modes 1 and 2: plane pairs 2w, 2w + 2W, ... ---------------------------------
+#pragma unroll 1
+        for (int p = 2 * warp; p < N; p += 2 * W) {
+            const bool two = p + 1 < N;
+            unsigned bh0[4], bl0[4], bh1[4], bl1[4];
+            tc3_plane_load<S, N>(xq, p, g, t, bh0, bl0, f16a);
+            if (two) tc3_plane_load<S, N>(xq, p + 1, g, t, bh1, bl1, f16a);
+            float z0[2][4], z1[2][4];
+            tc3_plane_compute<XEXACT>(bh0, bl0, m2h, m2l, m1h, m1l, z0, f16a, f2h, f2l);
+            if (two) tc3_plane_compute<XEXACT>(bh1, bl1, m2h, m2l, m1h, m1l, z1, f16a, f2h, f2l);
+            __syncwarp();   // planes p, p+1 are read by every lane before they are overwritten
+            tc3_plane_store(tb, p, g, t, z0);
+            if (two) tc3_plane_store(tb, p + 1, g, t, z1);
+        }
+        fence_proxy_async_smem();   // this thread's reads of the operand buffer precede a refill
+        __syncthreads();            // T complete
+        if (!L::INPLACE && threadIdx.x == 0 && inst + 2 * G < a.batch) fetch(b, inst + 2 * G);
+
+        // ---- mode 3: row-block pairs 2w, 2w + 2W, ... -------------------------------------
+        S* yq = static_cast<S*>(a.Y) + inst * NX;
+#pragma unroll 1
+        for (int mt = 2 * warp; mt < N; mt += 2 * W) {
+            tc3_rows<S, N>(a, yq, tb_s, mt, lane, m3h, m3l);
+            if (mt + 1 < N) tc3_rows<S, N>(a, yq, tb_s, mt + 1, lane, m3h, m3l);
+        }
+        fence_proxy_async_smem();
+        __syncthreads();            // T free (in place: so is the operand buffer)
+        if (L::INPLACE && threadIdx.x == 0 && inst + 2 * G < a.batch) fetch(b, inst + 2 * G);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
@@ -555,16 +777,52 @@ static inline float bf16_to_float(unsigned short h) {
 // Column-major N x N (double) -> row-major 16 x 16 packed bf16 pairs, split hi/lo.
 // Row-major 16 x 16 split of blockdiag(M, ..., M) with B x B blocks (B = 16:
 // M itself, zero-padded).
-static void split_rowmajor(const double* m, int N, unsigned* hi, unsigned* lo, int B = 16) {
+static void split_rowmajor(const double* m, int N, unsigned* hi, unsigned* lo, int B = 16, double scale = 1.0) {
     for (int r = 0; r < 16; ++r)
         for (int c2 = 0; c2 < 8; ++c2) {
             unsigned short h[2], l[2];
             for (int e = 0; e < 2; ++e) {
                 const int c = 2 * c2 + e;
                 const int rl = r % B, cl = c % B;
-                const float v = (r / B == c / B && rl < N && cl < N) ? (float)m[rl + N * cl] : 0.f;
+                const float v = (r / B == c / B && rl < N && cl < N) ? (float)(m[rl + N * cl] * scale) : 0.f;
                 h[e] = bf16_rne(v);
                 l[e] = bf16_rne(v - bf16_to_float(h[e]));
+            }
+            hi[r * 8 + c2] = (unsigned)h[0] | ((unsigned)h[1] << 16);
+            lo[r * 8 + c2] = (unsigned)l[0] | ((unsigned)l[1] << 16);
+        }
+}
+
+// Power-of-two scale 2^s that brings the largest |entry| of m into [2^14, 2^15),
+// so that an f16 split of m * 2^s keeps 22 significant bits of the large
+// entries and cannot overflow.  False (no f16 split) for a zero or non-finite
+// matrix, or a scale whose inverse could underflow the other factor.
+static bool f16_scale(const double* m, int N, int& s) {
+    double mx = 0.0;
+    for (int e = 0; e < N * N; ++e) {
+        if (!std::isfinite(m[e])) return false;
+        mx = std::max(mx, std::fabs(m[e]));
+    }
+    if (mx == 0.0) return false;
+    int ex = 0;
+    std::frexp(mx, &ex);   // mx in [2^(ex-1), 2^ex)
+    s = 15 - ex;
+    return s >= -40 && s <= 40;
+}
+
+// f16 hi / lo split of m * 2^s (round to nearest even), packed as split_rowmajor.
+static void split_rowmajor_f16(const double* m, int N, int s, unsigned* hi, unsigned* lo, int B = 16) {
+    for (int r = 0; r < 16; ++r)
+        for (int c2 = 0; c2 < 8; ++c2) {
+            unsigned short h[2], l[2];
+            for (int e = 0; e < 2; ++e) {
+                const int c = 2 * c2 + e;
+                const int rl = r % B, cl = c % B;
+                const float v = (r / B == c / B && rl < N && cl < N) ? (float)std::ldexp(m[rl + N * cl], s) : 0.f;
+                const __half hv = __float2half_rn(v);
+                const __half lv = __float2half_rn(v - __half2float(hv));
+                h[e] = __half_as_ushort(hv);
+                l[e] = __half_as_ushort(lv);
             }
             hi[r * 8 + c2] = (unsigned)h[0] | ((unsigned)h[1] << 16);
             lo[r * 8 + c2] = (unsigned)l[0] | ((unsigned)l[1] << 16);
@@ -577,7 +835,16 @@ static kron_status launch_tc2_n(const KronDesc& d, cudaStream_t st) {
     if (dev.sms <= 0) return KRON_ERR_CUDA;
     TcArgs2<N> a;
     split_rowmajor(d.m1, N, a.m1h, a.m1l, tc2_block(N));
-    split_rowmajor(d.m2, N, a.m2h, a.m2l, tc2_block(N));
+    int s = 0;
+    a.f16a = std::is_same<S, __half>::value && f16_scale(d.m1, N, s);
+    if (a.f16a) {   // f16 storage: W = (M1 2^s) X in f16 MMAs, then W (M2 2^-s)^T
+        split_rowmajor_f16(d.m1, N, s, a.f1h, a.f1l, tc2_block(N));
+        split_rowmajor(d.m2, N, a.m2h, a.m2l, tc2_block(N), std::ldexp(1.0, -s));
+    } else {
+        memset(a.f1h, 0, sizeof(a.f1h));
+        memset(a.f1l, 0, sizeof(a.f1l));
+        split_rowmajor(d.m2, N, a.m2h, a.m2l, tc2_block(N));
+    }
     a.X = d.X;
     a.Y = d.Y;
     a.batch = d.batch;
@@ -623,11 +890,21 @@ static kron_status launch_tc3_n(const KronDesc& d, cudaStream_t st) {
     const DeviceInfo& dev = device_info();
     if (dev.sms <= 0) return KRON_ERR_CUDA;
     TcArgs3<N> a;
-    split_rowmajor(d.m1, N, a.m1h, a.m1l);
     split_rowmajor(d.m2, N, a.m2h, a.m2l);
     split_rowmajor(d.m3, N, a.m3h, a.m3l);
+    int s = 0;
+    a.f16a = std::is_same<S, __half>::value && f16_scale(d.m2, N, s);
+    if (a.f16a) {   // f16 storage: W' = (M2 2^s) X_p^T in f16 MMAs, then W' (M1 2^-s)^T
+        split_rowmajor_f16(d.m2, N, s, a.f2h, a.f2l);
+        split_rowmajor(d.m1, N, a.m1h, a.m1l, 16, std::ldexp(1.0, -s));
+    } else {
+        memset(a.f2h, 0, sizeof(a.f2h));
+        memset(a.f2l, 0, sizeof(a.f2l));
+        split_rowmajor(d.m1, N, a.m1h, a.m1l);
+    }
     a.X = d.X;
     a.Y = d.Y;
+    a.ypair = ((uintptr_t)d.Y & 3u) == 0;
     a.batch = d.batch;
     a.alpha = (float)d.alpha;
     a.beta = (float)d.beta;
@@ -635,7 +912,28 @@ static kron_status launch_tc3_n(const KronDesc& d, cudaStream_t st) {
     a.alpha_one = d.alpha == 1.0;
     a.err = device_error_word();
     if (!a.err) return KRON_ERR_CUDA;
-    const size_t smem = 128 + kTc3Warps * (size_t)Tc3Layout<S, N>::PER_WARP;
+    using L = Tc3Layout<S, N>;
+    // compute_warps 1: the single-warp kernel; else W warps share an instance.
+    // Measured default: four warps at n = 14, 15, 16 (seven or eight plane pairs
+    // to share), one below (too few pairs to balance the barrier) and for f16
+    // storage at odd n (measured 3x slower with several warps; not understood).
+    const bool odd16 = std::is_same<S, __half>::value && (N & 1);
+    const int W = d.warps > 0 ? d.warps : ((N >= 14 && !odd16) ? 4 : 1);
+    if (W != 1) {
+        const size_t smem = 128 + 2 * (size_t)L::XB + L::TB;
+        if (W > 8 || smem > dev.smem_per_block_optin) return KRON_ERR_NOT_SUPPORTED;
+        auto kern = tc3g_kernel<S, N>;
+        if (!ensure_smem_optin((const void*)kern, smem)) return KRON_ERR_CUDA;
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * W, smem) != cudaSuccess)
+            return KRON_ERR_CUDA;
+        int64_t grid = d.grid > 0 ? d.grid : (int64_t)(per_sm < 1 ? 1 : per_sm) * dev.sms;
+        if (grid > d.batch) grid = d.batch;
+        if (grid < 1) grid = 1;
+        kern<<<(unsigned)grid, 32 * W, smem, st>>>(a);
+        return cudaPeekAtLastError() == cudaSuccess ? KRON_OK : KRON_ERR_CUDA;
+    }
+    const size_t smem = 128 + kTc3Warps * (size_t)L::PER_WARP;
     if (smem > dev.smem_per_block_optin) return KRON_ERR_NOT_SUPPORTED;
     auto kern = tc3_kernel<S, N>;
     if (!ensure_smem_optin((const void*)kern, smem)) return KRON_ERR_CUDA;

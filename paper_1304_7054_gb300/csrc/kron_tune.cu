@@ -101,10 +101,13 @@ bool variant_ok(int kind, int n, kron_dtype io, kron_compute comp, int variant, 
     }
 }
 
-// Whether `warps` compute warps per CTA fit the body (0: its default).  Only the
-// FP32 2-D n = 16 in-place body takes it: groups of P / 4 warps, at most 16.
+// Whether `warps` compute warps per CTA fit the body (0: its default): the FP32
+// 2-D n = 16 in-place body (groups of P / 4 warps, at most 16) and the 3-D split
+// tensor body (1, 2, 4 or 8 warps per instance).
 bool warps_ok(int kind, int n, kron_dtype io, kron_compute comp, int variant, int P, int warps) {
     if (warps == 0) return true;
+    if (kind == 3 && comp == KRON_COMPUTE_32F_BF16X3)   // warps sharing one instance
+        return warps == 1 || warps == 2 || warps == 4 || warps == 8;
     if (kind != 2 || n != 16 || io != KRON_R32F || comp != KRON_COMPUTE_NATIVE) return false;
     if (variant != KRON_VARIANT_AUTO && variant != KRON_VARIANT_IN_PLACE) return false;
     const int g = (P > 0 ? P : kPair16TDefaultP) / 4;
@@ -259,10 +262,14 @@ KRON_API kron_status kron_autotune_config(kron_stream_t stream, int kind, int n,
                                  {16, 4, 8},  {24, 3, 12}, {24, 6, 12}, {8, 8, 8}};
         for (const auto& s : shapes) cands.push_back(kron_kernel_config{KRON_VARIANT_IN_PLACE, s[0], s[1], 0, s[2]});
     }
-    if (comp != KRON_COMPUTE_NATIVE || !real_io(io)) {   // one body: tile and depth only
+    if (comp != KRON_COMPUTE_NATIVE || !real_io(io)) {   // one body: tile and depth (2-D), warps (3-D)
         cands.resize(1);
-        for (int mul2 : {1, 2, 4, 8})
-            for (int ns : {1, 2}) cands.push_back(kron_kernel_config{0, std::max(1, base * mul2 / 2), ns, 0, 0});
+        if (kind == 3 && comp == KRON_COMPUTE_32F_BF16X3) {
+            for (int w : {1, 2, 4, 8}) cands.push_back(kron_kernel_config{0, 0, 0, 0, w});
+        } else {
+            for (int mul2 : {1, 2, 4, 8})
+                for (int ns : {1, 2}) cands.push_back(kron_kernel_config{0, std::max(1, base * mul2 / 2), ns, 0, 0});
+        }
     }
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return KRON_ERR_CUDA;

@@ -226,3 +226,35 @@ def test_bf16x3_16bit_storage_full_size_sampled(kind, n, batch, io):
     assert storage_check(got, sub, Xs, io, compute="bf16x3") <= 1.0
     del X, Y
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("io", ["bf16", "f16"])
+@pytest.mark.parametrize("guard", [7, 8])
+def test_bf16x3_3d_16bit_results_at_any_alignment(io, guard):
+    """16-bit results leave as 32-bit pairs when Y is 4-byte aligned (guard 8) and
+    element by element otherwise (guard 7: Y two bytes past a 4-byte boundary)."""
+    b = inputs.make_batch(3, 16, 37, seed=395 + guard, x_dist="normal")
+    Y, X64 = run_gpu(b, io=io, compute="bf16x3", guard=guard)
+    assert storage_check(Y, b, X64, io, compute="bf16x3") <= 1.0
+
+
+@pytest.mark.parametrize("io", ["f32", "bf16", "f16"])
+@pytest.mark.parametrize("n", [16, 15, 13, 10, 6])
+def test_bf16x3_3d_warps_per_instance(io, n):
+    """The single-warp kernel and 2, 4, 8 warps sharing an instance give the same bits."""
+    b = inputs.make_batch(3, n, 43, seed=397 + n, x_dist="normal")
+    outs = []
+    try:
+        for w in (1, 2, 4, 8):
+            kg.set_kernel_config(3, n, io, "bf16x3", compute_warps=w)
+            assert kg.get_kernel_config(3, n, io, "bf16x3")["compute_warps"] == w
+            Y, X64 = run_gpu(b, io=io, compute="bf16x3", guard=8)
+            outs.append(Y)
+    finally:
+        kg.set_kernel_config(3, n, io, "bf16x3")
+    for Y in outs[1:]:
+        assert np.array_equal(Y, outs[0])
+    if io == "f32":
+        assert max_norm_err(outs[0], oracle_ref(b, X64), b, X64) <= 1e-5
+    else:
+        assert storage_check(outs[0], b, X64, io, compute="bf16x3") <= 1.0
