@@ -543,6 +543,8 @@ def kernel_of(kind, n, io, compute, variant="auto"):
     """Name of the kernel the library dispatches a contiguous batch to (with the
     kernel body the tuning table holds for it)."""
     if compute == "bf16x3":
+        if kind == 3 and n >= 14 and not (io == "f16" and n % 2):
+            return f"tc3g_kernel<n={n},{io}>"   # several warps share an instance
         return f"tc{kind}_kernel<n={n},{io}>"
     if io in ("c64", "c128") or variant == "scalar":
         return f"fiber_kernel<{io},n={n},{kind}-D>"
