@@ -295,13 +295,14 @@ KRON_API kron_status kron_autotune(kron_stream_t stream, int kind, int n, int64_
  *   fibers_per_step:    register blocking of the last contraction of the
  *                       packed-pair bodies: 1 or 2 fibers per thread and step
  *                       (0 = default)
- *   compute_warps:      compute warps per CTA (0 = default).  Two bodies
- *                       take it.  The FP32 2-D n = 16 in-place body: its
- *                       warps work in groups of instances_per_tile / 4, each
- *                       group on its own tile of the ring, so compute_warps
- *                       must be a multiple of that, at most 16; with
- *                       pipeline_depth (up to 12 tiles for that body, 8 for
- *                       the others) it sets the split of an SM between
+ *   compute_warps:      compute warps per CTA (0 = default).  The FP32 2-D
+ *                       in-place bodies take it -- n = 16: groups of
+ *                       instances_per_tile / 4 warps; n = 10, 14: groups of
+ *                       four warps; each group on its own tile of the ring,
+ *                       so compute_warps must be a multiple of the group,
+ *                       at most 16 -- and, with pipeline_depth (up to 12
+ *                       tiles for these bodies, 8 for the others), sets the
+ *                       split of an SM between
  *                       registers (resident warps) and shared memory (tiles
  *                       in flight).  The 3-D split tensor body
  *                       (KRON_COMPUTE_32F_BF16X3): 1 = one warp per instance

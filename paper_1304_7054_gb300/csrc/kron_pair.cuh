@@ -66,6 +66,31 @@ __device__ __forceinline__ void contract_rows(const f2* __restrict__ Mp, const f
     }
 }
 
+// bar.red.or over the 128 threads of compute group g (named barrier 1 + g).  The
+// barrier number is an immediate, so the kernel reserves five barriers, not all
+// sixteen (a CTA that reserves every barrier limits how many CTAs an SM holds).
+template <int ID>
+__device__ __forceinline__ bool bar_or_128(bool v) {
+    unsigned r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "bar.red.or.pred p, %2, 128, q;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(r)
+        : "r"((unsigned)v), "n"(ID)
+        : "memory");
+    return r != 0;
+}
+__device__ __forceinline__ bool group_sync_or(bool v, int g) {
+    switch (g) {
+        case 0: return bar_or_128<1>(v);
+        case 1: return bar_or_128<2>(v);
+        case 2: return bar_or_128<3>(v);
+        default: return bar_or_128<4>(v);
+    }
+}
+
 template <int N, int D>
 struct PairArgs {
     f2 da[N * N];                  // first stage component, duplicated (2-D: M2, 3-D: M3)

@@ -426,7 +426,7 @@ constexpr int kHWBytes = kTileWords * 4;         // W: the FP32 tile layout
 __device__ __forceinline__ int hslot_words(int q) { return kHSlotWords * q + 4 * ((q >> 2) & 1); }
 
 template <typename S>
-__global__ void __launch_bounds__(kThreads, 6) pair16h_kernel(const __grid_constant__ PairArgs<kN, 2> a) {
+__global__ void __launch_bounds__(kThreads) pair16h_kernel(const __grid_constant__ PairArgs<kN, 2> a) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
     uint64_t* empty = full + kMaxRing;

@@ -27,9 +27,10 @@ namespace kron {
 
 namespace {
 
-constexpr int kIpCompute = 128;               // compute threads (4 warps)
+constexpr int kIpCompute = 128;               // compute threads of one group (4 warps)
 constexpr int kIpThreads = kIpCompute + 32;   // + one producer warp
-constexpr int kIpMaxRing = 4;
+constexpr int kIpMaxRing = 12;
+constexpr int kIpMaxGroups = 4;
 
 template <int N>
 struct IpLayout {
@@ -39,7 +40,10 @@ struct IpLayout {
     static constexpr int G2 = N / 2;              // same, stage 2
     // default tile and ring depth (measured on the bench batches)
     static constexpr int P0 = N == 10 ? 48 : 40;
-    static constexpr int NB0 = N == 10 ? 1 : 2;
+    // default ring depth and compute warps (measured: one CTA per SM with four
+    // groups and a deep ring streams best)
+    static constexpr int NB0 = N == 10 ? 10 : 5;
+    static constexpr int W0 = 16;
 };
 
 template <int N>
@@ -52,22 +56,28 @@ __device__ __forceinline__ void load_col(const float* p, float (&w)[N]) {
     }
 }
 
+// A CTA holds G compute groups of four warps and one producer warp; group g
+// takes the CTA's tiles it = g mod G from one shared ring, so one CTA per SM
+// can keep a deep ring in flight while its groups work.
 template <int N>
-__global__ void __launch_bounds__(kIpThreads, 6) pair2ip_kernel(const __grid_constant__ PairArgs<N, 2> a) {
+__global__ void __launch_bounds__(kIpCompute * kIpMaxGroups + 32, 1) pair2ip_kernel(const __grid_constant__ PairArgs<N, 2> a,
+                                                                                     int G) {
     using L = IpLayout<N>;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
     uint64_t* empty = full + kIpMaxRing;
-    float* ring = reinterpret_cast<float*>(smem + 128);
+    float* ring = reinterpret_cast<float*>(smem + 256);
     const int NB = a.nstage;
     const int P = a.P;             // a multiple of 8
     const int QG = P >> 3;
     const int tile_words = P * L::NX;
-    const int tid = threadIdx.x;
+    const int ncompute = kIpCompute * G;
+    const int gidx = threadIdx.x / kIpCompute;
+    const int tid = threadIdx.x - kIpCompute * gidx;   // thread within its group (producer: lane + 128)
     const int64_t ntiles = (a.batch + P - 1) / P;
     const int64_t grid = gridDim.x;
 
-    if (tid == 0) {
+    if (threadIdx.x == 0) {
         for (int s = 0; s < NB; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], kIpCompute);
@@ -76,11 +86,11 @@ __global__ void __launch_bounds__(kIpThreads, 6) pair2ip_kernel(const __grid_con
     }
     __syncthreads();
 
-    if (tid >= kIpCompute) {
+    if (threadIdx.x >= ncompute) {
         // Producer: tile `it` goes to buffer it % NB once the compute threads have
         // released that buffer's previous tile (it - NB), whose results they left
         // in the buffer: those are stored first.
-        const int lane = tid - kIpCompute;
+        const int lane = threadIdx.x - ncompute;
         const uint64_t pol = l2_evict_first_policy();
         float* Y = static_cast<float*>(a.Y);
         const float* X = static_cast<const float*>(a.X);
@@ -121,8 +131,8 @@ __global__ void __launch_bounds__(kIpThreads, 6) pair2ip_kernel(const __grid_con
 
     const f2* m1p = reinterpret_cast<const f2*>(a.m1);
     const float* Y = static_cast<const float*>(a.Y);
-    int it = 0;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += grid, ++it) {
+    for (int it = gidx; blockIdx.x + (int64_t)it * grid < ntiles; it += G) {
+        const int64_t tile = blockIdx.x + (int64_t)it * grid;
         const int s = it % NB;
         float* buf = ring + s * tile_words;
         const int64_t inst0 = tile * P;
@@ -145,7 +155,7 @@ __global__ void __launch_bounds__(kIpThreads, 6) pair2ip_kernel(const __grid_con
                 for (int j = 0; j < N; ++j) *reinterpret_cast<f2*>(p + N * j) = w[j];
             }
         }
-        if (compute_sync_or(!ok)) {
+        if (group_sync_or(!ok, gidx)) {
             // A copy did not land in time: wait (bounded) for the ones that may still
             // be in flight into this CTA's buffers, then give up.  The producer cannot
             // issue beyond tile it + NB - 1, whose buffer this iteration still holds.
@@ -189,7 +199,7 @@ __global__ void __launch_bounds__(kIpThreads, 6) pair2ip_kernel(const __grid_con
 
 template <int N>
 size_t ip_smem_bytes(int P, int nb) {
-    return 128 + (size_t)nb * P * IpLayout<N>::NX * sizeof(float);
+    return 256 + (size_t)nb * P * IpLayout<N>::NX * sizeof(float);
 }
 
 template <int N>
@@ -220,7 +230,10 @@ kron_status launch_ip_n(const KronDesc& d, cudaStream_t st) {
     a.err = device_error_word();
     if (!a.err) return KRON_ERR_CUDA;
     const int P = d.P > 0 ? d.P : L::P0;
-    int nb = d.nstage >= 1 ? d.nstage : L::NB0;
+    const int W = d.warps > 0 ? d.warps : L::W0;
+    const int G = W / 4;
+    if (G < 1 || G > kIpMaxGroups || (W % 4)) return KRON_ERR_NOT_SUPPORTED;
+    int nb = d.nstage >= 1 ? d.nstage : (d.warps > 0 || d.P > 0 ? 2 * G : L::NB0);
     if (nb > kIpMaxRing) nb = kIpMaxRing;
     size_t smem = ip_smem_bytes<N>(P, nb);
     while (nb > 1 && smem > dev.smem_per_block_optin) smem = ip_smem_bytes<N>(P, --nb);
@@ -229,17 +242,18 @@ kron_status launch_ip_n(const KronDesc& d, cudaStream_t st) {
     a.nstage = nb;
     auto kern = pair2ip_kernel<N>;
     if (!ensure_smem_optin((const void*)kern, smem)) return KRON_ERR_CUDA;
+    const int threads = kIpCompute * G + 32;
     const int64_t ntiles = (d.batch + P - 1) / P;
     int64_t grid = d.grid;
     if (grid <= 0) {
         int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kIpThreads, smem) != cudaSuccess)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) != cudaSuccess)
             return KRON_ERR_CUDA;
         grid = (int64_t)(per_sm < 1 ? 1 : per_sm) * dev.sms;
     }
     if (grid > ntiles) grid = ntiles;
     if (grid < 1) grid = 1;
-    kern<<<(unsigned)grid, kIpThreads, smem, st>>>(a);
+    kern<<<(unsigned)grid, threads, smem, st>>>(a, G);
     return cudaPeekAtLastError() == cudaSuccess ? KRON_OK : KRON_ERR_CUDA;
 }
 

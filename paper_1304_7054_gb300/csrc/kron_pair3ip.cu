@@ -39,7 +39,7 @@ constexpr int kMaxRing = 4;
 
 __device__ __forceinline__ int at(int i, int j, int k) { return i + 16 * j + kPlane * k; }
 
-__global__ void __launch_bounds__(kThreads, 5) pair3ip_kernel(const __grid_constant__ PairArgs<kN, 3> a) {
+__global__ void __launch_bounds__(kThreads) pair3ip_kernel(const __grid_constant__ PairArgs<kN, 3> a) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
     uint64_t* empty = full + kMaxRing;

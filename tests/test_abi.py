@@ -222,6 +222,9 @@ def test_kernel_config_validation_and_round_trip(lib):
     assert lib.kron_set_kernel_config(2, 12, f32, 0, ctypes.byref(cfg(0, 0, 0, 0, 8))) == NOTSUP_
     assert lib.kron_set_kernel_config(2, 16, kg.DTYPES["bf16"], 0, ctypes.byref(cfg(1, 16, 0, 0, 4))) == NOTSUP_
     assert lib.kron_set_kernel_config(3, 16, f32, 1, ctypes.byref(cfg(0, 0, 0, 0, 3))) == NOTSUP_   # 1, 2, 4, 8
+    assert lib.kron_set_kernel_config(2, 10, f32, 0, ctypes.byref(cfg(1, 48, 10, 0, 6))) == NOTSUP_  # groups of 4
+    assert lib.kron_set_kernel_config(2, 10, f32, 0, ctypes.byref(cfg(1, 48, 10, 0, 16))) == 0
+    assert lib.kron_set_kernel_config(2, 10, f32, 0, ctypes.byref(cfg())) == 0
     assert lib.kron_set_kernel_config(3, 16, f32, 1, ctypes.byref(cfg(0, 0, 0, 0, 8))) == 0
     assert lib.kron_set_kernel_config(3, 16, f32, 1, ctypes.byref(cfg())) == 0
     assert lib.kron_set_kernel_config(2, 16, f32, 0, ctypes.byref(cfg(1, 24, 3, 0, 12))) == 0
