@@ -300,7 +300,9 @@ KRON_API kron_status kron_autotune(kron_stream_t stream, int kind, int n, int64_
  *                       instances_per_tile / 4 warps; n = 10, 14: groups of
  *                       four warps; each group on its own tile of the ring,
  *                       so compute_warps must be a multiple of the group,
- *                       at most 16 -- and, with pipeline_depth (up to 12
+ *                       at most 16; pipeline_depth is then rounded down to
+ *                       a multiple of the number of groups (at least one
+ *                       tile per group) -- and, with pipeline_depth (up to 12
  *                       tiles for these bodies, 8 for the others), sets the
  *                       split of an SM between
  *                       registers (resident warps) and shared memory (tiles

@@ -596,11 +596,17 @@ kron_status launch_pair16(const KronDesc& d, cudaStream_t st) {
             const int groups = warps / (P / 4);
             if (groups < 1 || warps % (P / 4) || warps > kTMaxWarps) return KRON_ERR_NOT_SUPPORTED;
             ta.groups = groups;
+            // The ring depth is a multiple of the number of groups: buffer it % NB
+            // then always passes from a group to the same group (tile it - NB), so
+            // a group starts its parity wait on a buffer only after its own
+            // previous use of it has completed (a parity wait cannot tell phase u
+            // from phase u - 2).
             int nb = d.nstage >= 1 ? d.nstage : 2 * groups;
             if (nb > kTMaxRing) nb = kTMaxRing;
-            if (nb < groups) nb = groups;
+            nb = nb < groups ? groups : nb / groups * groups;
+            if (nb > kTMaxRing) return KRON_ERR_NOT_SUPPORTED;
             size_t smem = pair16t_smem_bytes(P, nb);
-            while (nb > 1 && smem > dev.smem_per_block_optin) smem = pair16t_smem_bytes(P, --nb);
+            while (nb > groups && smem > dev.smem_per_block_optin) smem = pair16t_smem_bytes(P, nb -= groups);
             if (smem > dev.smem_per_block_optin) return KRON_ERR_NOT_SUPPORTED;
             a.P = P;
             a.nstage = nb;

@@ -40,10 +40,12 @@ struct IpLayout {
     static constexpr int G2 = N / 2;              // same, stage 2
     // default tile and ring depth (measured on the bench batches)
     static constexpr int P0 = N == 10 ? 48 : 40;
-    // default ring depth and compute warps (measured: one CTA per SM with four
-    // groups and a deep ring streams best)
-    static constexpr int NB0 = N == 10 ? 10 : 5;
-    static constexpr int W0 = 16;
+    // default ring depth and compute warps (measured: at n = 10 one CTA per SM
+    // with four groups and an 8-deep ring streams best; at n = 14 the 31 KB tiles
+    // leave room for one tile per group only, and six CTAs of one group with two
+    // buffers each are faster)
+    static constexpr int NB0 = N == 10 ? 8 : 2;
+    static constexpr int W0 = N == 10 ? 16 : 4;
 };
 
 template <int N>
@@ -233,10 +235,15 @@ kron_status launch_ip_n(const KronDesc& d, cudaStream_t st) {
     const int W = d.warps > 0 ? d.warps : L::W0;
     const int G = W / 4;
     if (G < 1 || G > kIpMaxGroups || (W % 4)) return KRON_ERR_NOT_SUPPORTED;
+    // The ring depth is a multiple of the number of groups, so that buffer it % NB
+    // passes from a group to the same group (tile it - NB): a group then starts
+    // its parity wait on a buffer only after its own previous use completed (a
+    // parity wait cannot tell phase u from phase u - 2).
     int nb = d.nstage >= 1 ? d.nstage : (d.warps > 0 || d.P > 0 ? 2 * G : L::NB0);
     if (nb > kIpMaxRing) nb = kIpMaxRing;
+    nb = nb < G ? G : nb / G * G;
     size_t smem = ip_smem_bytes<N>(P, nb);
-    while (nb > 1 && smem > dev.smem_per_block_optin) smem = ip_smem_bytes<N>(P, --nb);
+    while (nb > G && smem > dev.smem_per_block_optin) smem = ip_smem_bytes<N>(P, nb -= G);
     if (smem > dev.smem_per_block_optin) return KRON_ERR_NOT_SUPPORTED;
     a.P = P;
     a.nstage = nb;
