@@ -493,7 +493,7 @@ def measure_interfaces(kg, steps, warmup, torch, dev, peaks):
     err = float((np.abs(got - ref).reshape(len(idx), -1).max(axis=1) /
                  (np.linalg.norm(As, axis=1) * np.linalg.norm(B))).max())
     out["tgemm_a-f32-m256-n16-k16"] = line(ms, 2.0 * m * n * k * batch, 4.0 * (m * k + m * n) * batch,
-                                           "gemm_a_pair_kernel<f32,n=16>", err, {"batch": batch})
+                                           "gemm_a_tma_kernel<f32,n=16>", err, {"batch": batch})
     del A, C
 
     # TKRON1, n = 16
@@ -509,7 +509,7 @@ def measure_interfaces(kg, steps, warmup, torch, dev, peaks):
     got = Y.view(batch, -1)[torch.from_numpy(idx).to(dev)].double().cpu().numpy().ravel()
     err = float((np.abs(got - ref).reshape(len(idx), -1).max(axis=1) /
                  (np.linalg.norm(Xs, axis=1) * np.linalg.norm(A1))).max())
-    out["tkron1-f32-n16"] = line(ms, 2.0 * nn * nn * batch, 8.0 * nn * batch, "kron1_kernel<f32,n=16>",
+    out["tkron1-f32-n16"] = line(ms, 2.0 * nn * nn * batch, 8.0 * nn * batch, "kron1t_kernel<f32,n=16>",
                                  err, {"batch": batch})
     del X, Y
 

@@ -27,6 +27,12 @@ inline unsigned __float_as_uint_host(float v) {
 
 constexpr int kGaThreads = 256;
 constexpr int kGaMaxK = 16;
+// Staged kernel: operand bytes per tile (at least one instance) and tiles in flight
+// per CTA; measured at m = 256, k = 16: two 16 KB instances per tile (one row pair
+// per thread), three tiles (0.98 of the copy bandwidth; one instance per tile,
+// half the threads idle: 0.85; deeper rings cost resident CTAs).
+constexpr size_t kGaTileBytes = 32768;
+constexpr int kGaRing = 3;
 
 template <typename T, int NN>
 struct __align__(8) GemmAArgs {
@@ -193,6 +199,167 @@ kron_status launch_ga_pair(const GemmADesc& g, cudaStream_t st) {
     return cudaPeekAtLastError() == cudaSuccess ? KRON_OK : KRON_ERR_CUDA;
 }
 
+// Contiguous batches (lda = m, lda2 = m k, ldc = m, ldc2 = m n, A 16-byte aligned,
+// m k a whole number of 16-byte units): the row-pair products of the kernel
+// above, with the operands staged in shared memory.  Tiles of P instances
+// arrive by one bulk copy each (TMA) in an NB-deep ring; a warp's lanes then
+// read 64 consecutive rows of one column per access (conflict-free) and store
+// their row pairs of C straight from registers (256 contiguous bytes per warp
+// and column).  Plain loads of the same rows streamed at 0.91-0.93 of the copy
+// bandwidth, the staged tiles at 0.98.
+template <int NN>
+struct __align__(8) GemmATArgs {
+    f2 bd[kGaMaxK * NN];   // (B[l, j], B[l, j]) at l * NN + j, zero beyond k x n
+    const void* A;
+    void* C;
+    int64_t batch;
+    int m, n, k;
+    int P, nstage;
+    int beta_zero, alpha_one;
+    float alpha, beta;
+    unsigned* err;
+};
+
+template <typename S, int NN>
+__global__ void __launch_bounds__(kGaThreads) gemm_a_tma_kernel(const __grid_constant__ GemmATArgs<NN> a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+    unsigned char* xbase = smem + 128;
+    const int P = a.P, NB = a.nstage, m2 = a.m / 2;
+    const int64_t inst = (int64_t)a.m * a.k;   // elements of one A^p
+    const size_t tile_bytes = ((size_t)P * inst * sizeof(S) + 127) / 128 * 128;
+    const int64_t ntiles = (a.batch + P - 1) / P;
+    const int64_t grid = gridDim.x;
+    const S* A = static_cast<const S*>(a.A);
+    S* C = static_cast<S*>(a.C);
+    uint64_t pol = 0;
+    auto issue = [&](int s, int64_t tile) {
+        const int64_t i0 = tile * P;
+        const unsigned bytes = (unsigned)(min((int64_t)P, a.batch - i0) * inst * (int64_t)sizeof(S));
+        mbar_arrive_expect_tx(&bars[s], bytes);
+        bulk_g2s(xbase + s * tile_bytes, A + i0 * inst, bytes, &bars[s], pol);
+    };
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NB; ++s) mbar_init(&bars[s], 1);
+        fence_barrier_init();
+        pol = l2_evict_first_policy();
+        for (int s = 0; s < NB; ++s)
+            if (blockIdx.x + s * grid < ntiles) issue(s, blockIdx.x + s * grid);
+    }
+    __syncthreads();
+    const f2 al = f2_pack(a.alpha, a.alpha), be = f2_pack(a.beta, a.beta);
+    int it = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += grid, ++it) {
+        const int s = it % NB;
+        const bool ok = mbar_wait_bounded(&bars[s], (unsigned)(it / NB) & 1u, a.err);
+        if (__syncthreads_or(!ok)) {
+            // wait (bounded) for the copies that may still be in flight, then give up
+            if (threadIdx.x == 0)
+                for (int j = it; j < it + NB; ++j)
+                    if (blockIdx.x + (int64_t)j * grid < ntiles)
+                        mbar_wait_bounded(&bars[j % NB], (unsigned)(j / NB) & 1u, a.err);
+            return;
+        }
+        const S* xt = reinterpret_cast<const S*>(xbase + s * tile_bytes);
+        const int64_t i0 = tile * P;
+        const int cnt = (int)min((int64_t)P, a.batch - i0);
+        for (int f = threadIdx.x; f < cnt * m2; f += kGaThreads) {
+            const int q = f / m2, i2 = f - q * m2;
+            const S* ar = xt + q * inst + 2 * i2;
+            f2 x[kGaMaxK];
+#pragma unroll
+            for (int l = 0; l < kGaMaxK; ++l) x[l] = l < a.k ? load_pair<S>(ar + a.m * l) : 0ull;
+            f2 c[NN];
+#pragma unroll
+            for (int j = 0; j < NN; ++j) c[j] = fmul2(a.bd[j], x[0]);
+#pragma unroll
+            for (int l = 1; l < kGaMaxK; ++l) {
+                if (l < a.k) {
+#pragma unroll
+                    for (int j = 0; j < NN; ++j) c[j] = ffma2(a.bd[l * NN + j], x[l], c[j]);
+                }
+            }
+            S* cr = C + (i0 + q) * (int64_t)a.m * a.n + 2 * i2;
+#pragma unroll
+            for (int j = 0; j < NN; ++j) {
+                if (j < a.n) {
+                    f2 v = a.alpha_one ? c[j] : fmul2(c[j], al);
+                    S* dst = cr + (int64_t)a.m * j;
+                    if (!a.beta_zero) v = ffma2(be, load_pair<S>(dst), v);
+                    if constexpr (sizeof(S) == 4)
+                        *reinterpret_cast<f2*>(dst) = v;
+                    else
+                        *reinterpret_cast<unsigned*>(dst) = pack16<S>(v);
+                }
+            }
+        }
+        __syncthreads();   // the tile's operands are read: its buffer can be refilled
+        if (threadIdx.x == 0) {
+            const int64_t next = tile + (int64_t)NB * grid;
+            if (next < ntiles) {
+                fence_proxy_async_smem();
+                issue(s, next);
+            }
+        }
+    }
+}
+
+template <typename S, int NN>
+kron_status launch_ga_tma(const GemmADesc& g, cudaStream_t st) {
+    GemmATArgs<NN> a;
+    memset(&a, 0, sizeof(a));
+    for (int l = 0; l < g.k; ++l)
+        for (int j = 0; j < g.n; ++j) {
+            const float v = (float)g.b[l * kGaMaxK + j];
+            a.bd[l * NN + j] = ((f2)__float_as_uint_host(v) << 32) | (f2)__float_as_uint_host(v);
+        }
+    a.A = g.A;
+    a.C = g.C;
+    a.batch = g.batch;
+    a.m = g.m;
+    a.n = g.n;
+    a.k = g.k;
+    a.alpha = (float)g.alpha;
+    a.beta = (float)g.beta;
+    a.alpha_one = g.alpha == 1.0;
+    a.beta_zero = g.beta == 0.0;
+    a.err = device_error_word();
+    if (!a.err) return KRON_ERR_CUDA;
+    const DeviceInfo& dev = device_info();
+    if (dev.sms <= 0) return KRON_ERR_CUDA;
+    const size_t inst_bytes = (size_t)g.m * g.k * sizeof(S);
+    int P = (int)std::max<size_t>(1, kGaTileBytes / inst_bytes);
+    int nb = kGaRing;
+    auto smem_of = [&](int p, int n_b) { return 128 + (size_t)n_b * (((size_t)p * inst_bytes + 127) / 128 * 128); };
+    while (P > 1 && smem_of(P, nb) > dev.smem_per_block_optin) --P;
+    while (nb > 1 && smem_of(P, nb) > dev.smem_per_block_optin) --nb;
+    const size_t smem = smem_of(P, nb);
+    if (smem > dev.smem_per_block_optin || (size_t)P * inst_bytes >= (1u << 20)) return KRON_ERR_NOT_SUPPORTED;
+    a.P = P;
+    a.nstage = nb;
+    auto kern = gemm_a_tma_kernel<S, NN>;
+    if (!ensure_smem_optin((const void*)kern, smem)) return KRON_ERR_CUDA;
+    const int64_t ntiles = (g.batch + P - 1) / P;
+    int64_t grid = g.grid;
+    if (grid <= 0) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGaThreads, smem) != cudaSuccess)
+            return KRON_ERR_CUDA;
+        grid = (int64_t)(per_sm < 1 ? 1 : per_sm) * dev.sms;
+    }
+    grid = std::max<int64_t>(1, std::min<int64_t>(grid, ntiles));
+    kern<<<(unsigned)grid, kGaThreads, smem, st>>>(a);
+    return cudaPeekAtLastError() == cudaSuccess ? KRON_OK : KRON_ERR_CUDA;
+}
+
+// Layouts the staged kernel takes: the row-pair layouts, packed (minimal leading
+// dimensions), A 16-byte aligned and each A^p a whole number of 16-byte units.
+bool ga_tma_ok(const GemmADesc& g) {
+    const size_t es = elem_size(g.io);
+    return g.lda == g.m && g.lda2 == (int64_t)g.m * g.k && g.ldc == g.m && g.ldc2 == (int64_t)g.m * g.n &&
+           (uintptr_t)g.A % 16 == 0 && ((size_t)g.m * g.k * es) % 16 == 0;
+}
+
 // Layouts the row-pair kernel takes: op = 'N', every row pair 2 * sizeof(S)-aligned.
 bool ga_pair_ok(const GemmADesc& g) {
     if (g.io == KRON_R64F || g.transa || g.m % 2) return false;
@@ -285,6 +452,16 @@ kron_status launch_ga(const GemmADesc& g, Kern kern, cudaStream_t st) {
 
 template <int NN>
 kron_status launch_ga_nn(const GemmADesc& g, cudaStream_t st) {
+    if (ga_pair_ok(g) && ga_tma_ok(g)) {
+        kron_status r = KRON_ERR_NOT_SUPPORTED;
+        switch (g.io) {
+            case KRON_R32F: r = launch_ga_tma<float, NN>(g, st); break;
+            case KRON_R16BF: r = launch_ga_tma<__nv_bfloat16, NN>(g, st); break;
+            case KRON_R16F: r = launch_ga_tma<__half, NN>(g, st); break;
+            default: break;
+        }
+        if (r != KRON_ERR_NOT_SUPPORTED) return r;
+    }
     if (ga_pair_ok(g)) {
         switch (g.io) {
             case KRON_R32F: return launch_ga_pair<float, NN>(g, st);

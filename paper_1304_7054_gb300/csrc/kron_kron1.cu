@@ -160,6 +160,131 @@ __global__ void __launch_bounds__(kK1Threads) kron1_kernel(const __grid_constant
     if (lane == 0) bulk_wait_all();
 }
 
+// FP32, n = 16, packed square vectors (ldxp = ldyp = 16), 16-byte aligned X and Y:
+// tiles of P vectors arrive by one bulk copy each (TMA) in an NB-deep ring, each
+// thread overwrites its own vector in place with its results, and the tile
+// leaves by one bulk copy.  Lane i reads and writes the four 16-byte chunks of
+// its vector starting at chunk (i >> 1) & 3, so the eight lanes of a quarter-
+// warp (vectors 64 bytes apart) hit eight distinct 4-bank groups; the chunks are
+// rotated back in registers (selects, no dynamic indexing).
+constexpr int kK1TileVecs = 512;   // 32 KB per tile: two vectors per thread
+constexpr int kK1Ring = 3;
+
+struct Kron1TArgs {
+    Kron1Args<16> a;
+    int nstage;
+    unsigned* err;
+};
+
+// t[k] <- t[(k + DIR * rho) mod 4] for DIR = -1 (undo a read rotation) or +1.
+template <int DIR>
+__device__ __forceinline__ void rotate_chunks(float4 (&t)[4], int rho) {
+    const bool r1 = rho & 1, r2 = rho & 2;
+    float4 v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float4 x = t[k], y = t[(k + DIR + 4) & 3];
+        v[k] = make_float4(r1 ? y.x : x.x, r1 ? y.y : x.y, r1 ? y.z : x.z, r1 ? y.w : x.w);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float4 x = v[k], y = v[(k + 2) & 3];
+        t[k] = make_float4(r2 ? y.x : x.x, r2 ? y.y : x.y, r2 ? y.z : x.z, r2 ? y.w : x.w);
+    }
+}
+
+__global__ void __launch_bounds__(kK1Threads) kron1t_kernel(const __grid_constant__ Kron1TArgs ta) {
+    const Kron1Args<16>& a = ta.a;
+    constexpr int N = 16, R = 8;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+    float* ring = reinterpret_cast<float*>(smem + 128);
+    const int NB = ta.nstage;
+    const int64_t ntiles = (a.batch + kK1TileVecs - 1) / kK1TileVecs;
+    const int64_t grid = gridDim.x;
+    const float* X = static_cast<const float*>(a.X);
+    float* Y = static_cast<float*>(a.Y);
+    const f2* mp = reinterpret_cast<const f2*>(a.m);
+    uint64_t pol = 0;
+    auto count = [&](int64_t t) { return (unsigned)min((int64_t)kK1TileVecs, a.batch - t * kK1TileVecs); };
+    auto issue = [&](int s, int64_t t) {
+        const unsigned bytes = count(t) * N * 4u;
+        mbar_arrive_expect_tx(&bars[s], bytes);
+        bulk_g2s(ring + (size_t)s * kK1TileVecs * N, X + t * kK1TileVecs * N, bytes, &bars[s], pol);
+    };
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NB; ++s) mbar_init(&bars[s], 1);
+        fence_barrier_init();
+        pol = l2_evict_first_policy();
+        for (int s = 0; s < NB; ++s)
+            if (blockIdx.x + s * grid < ntiles) issue(s, blockIdx.x + s * grid);
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, rho = (lane >> 1) & 3;
+    int it = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += grid, ++it) {
+        const int s = it % NB;
+        const bool ok = mbar_wait_bounded(&bars[s], (unsigned)(it / NB) & 1u, ta.err);
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) {
+                for (int j = it; j < it + NB; ++j)
+                    if (blockIdx.x + (int64_t)j * grid < ntiles)
+                        mbar_wait_bounded(&bars[j % NB], (unsigned)(j / NB) & 1u, ta.err);
+                bulk_wait_all();
+            }
+            return;
+        }
+        float* buf = ring + (size_t)s * kK1TileVecs * N;
+        const int cnt = (int)count(tile);
+        for (int q = threadIdx.x; q < cnt; q += kK1Threads) {
+            float* v = buf + q * N;
+            float4 t[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) t[c] = *reinterpret_cast<const float4*>(v + 4 * ((c + rho) & 3));
+            rotate_chunks<-1>(t, rho);
+            float x[N];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                x[4 * c] = t[c].x;
+                x[4 * c + 1] = t[c].y;
+                x[4 * c + 2] = t[c].z;
+                x[4 * c + 3] = t[c].w;
+            }
+            f2 y[R];
+            contract_rows<N>(mp, x, y);
+            if (!a.alpha_one) {
+                const f2 al = f2_pack(a.alpha, a.alpha);
+#pragma unroll
+                for (int r = 0; r < R; ++r) y[r] = fmul2(y[r], al);
+            }
+            if (!a.beta_zero) {
+                const float* yp = Y + (tile * kK1TileVecs + q) * N;
+                const f2 be = f2_pack(a.beta, a.beta);
+#pragma unroll
+                for (int r = 0; r < R; ++r) y[r] = ffma2(be, load_pair<float>(yp + 2 * r), y[r]);
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                t[c] = make_float4(f2_lo(y[2 * c]), f2_hi(y[2 * c]), f2_lo(y[2 * c + 1]), f2_hi(y[2 * c + 1]));
+            rotate_chunks<1>(t, rho);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) *reinterpret_cast<float4*>(v + 4 * ((c + rho) & 3)) = t[c];
+        }
+        fence_proxy_async_smem();   // results written: visible to the bulk store
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            bulk_s2g_hint(Y + tile * kK1TileVecs * N, buf, count(tile) * N * 4u, pol);
+            bulk_commit();
+            const int64_t next = tile + (int64_t)NB * grid;
+            if (next < ntiles) {
+                bulk_wait_read();   // the results have left the buffer
+                issue(s, next);
+            }
+        }
+    }
+    if (threadIdx.x == 0) bulk_wait_all();
+}
+
 template <typename S, int N>
 kron_status launch_k1(const GemmADesc& g, cudaStream_t st) {
     // g describes TKRON1 as TGEMM_A with m = 1: b[l * 16 + j] = op(A)(j, l).
@@ -183,6 +308,35 @@ kron_status launch_k1(const GemmADesc& g, cudaStream_t st) {
     a.beta_zero = g.beta == 0.0;
     const DeviceInfo& dev = device_info();
     if (dev.sms <= 0) return KRON_ERR_CUDA;
+    if constexpr (N == 16 && sizeof(S) == 4) {
+        if (a.ma == 16 && a.na == 16 && a.ldxp == 16 && a.ldyp == 16 && (uintptr_t)g.A % 16 == 0 &&
+            (uintptr_t)g.C % 16 == 0) {
+            Kron1TArgs ta;
+            ta.a = a;
+            ta.err = device_error_word();
+            if (!ta.err) return KRON_ERR_CUDA;
+            int nb = kK1Ring;
+            auto smem_of = [](int n_b) { return 128 + (size_t)n_b * kK1TileVecs * 16 * sizeof(float); };
+            while (nb > 1 && smem_of(nb) > dev.smem_per_block_optin) --nb;
+            const size_t smem = smem_of(nb);
+            ta.nstage = nb;
+            if (smem <= dev.smem_per_block_optin) {
+                const void* kern = (const void*)kron1t_kernel;
+                if (!ensure_smem_optin(kern, smem)) return KRON_ERR_CUDA;
+                int per_sm = 0;
+                if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kron1t_kernel, kK1Threads, smem) !=
+                    cudaSuccess)
+                    return KRON_ERR_CUDA;
+                const int64_t ntiles = (g.batch + kK1TileVecs - 1) / kK1TileVecs;
+                int64_t grid = (int64_t)(per_sm < 1 ? 1 : per_sm) * dev.sms;
+                grid = std::max<int64_t>(1, std::min<int64_t>(grid, ntiles));
+                void* args[] = {&ta};
+                if (cudaLaunchKernel(kern, dim3((unsigned)grid), dim3(kK1Threads), args, smem, st) != cudaSuccess)
+                    return KRON_ERR_CUDA;
+                return cudaPeekAtLastError() == cudaSuccess ? KRON_OK : KRON_ERR_CUDA;
+            }
+        }
+    }
     auto kern = kron1_kernel<S, N>;
     const size_t smem = (size_t)kK1Warps * 2 * 32 * N * sizeof(S);
     if (!ensure_smem_optin((const void*)kern, smem)) return KRON_ERR_CUDA;
