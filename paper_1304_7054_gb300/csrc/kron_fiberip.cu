@@ -25,9 +25,15 @@ namespace kron {
 
 namespace {
 
-constexpr int kFiCompute = 128;
+constexpr int kFiCompute = 128;                 // compute threads of one group (4 warps)
 constexpr int kFiThreads = kFiCompute + 32;
-constexpr int kFiMaxRing = 4;
+constexpr int kFiMaxRing = 12;
+constexpr int kFiMaxGroups = 4;
+// 2-D: up to four compute groups share one CTA's ring (one CTA per SM); 3-D:
+// one group per CTA, several CTAs per SM (the FMA-bound 3-D stages want the
+// resident warps of more CTAs).
+template <int D> constexpr int fi_max_threads() { return D == 2 ? kFiCompute * kFiMaxGroups + 32 : kFiThreads; }
+template <int D> constexpr int fi_min_blocks() { return D == 2 ? 1 : 4; }
 
 template <int N>
 struct FiberIpArgs {
@@ -70,19 +76,22 @@ __device__ __forceinline__ void fiber_in_place(float* p, const f2* Mp) {
 }
 
 template <int N, int D>
-__global__ void __launch_bounds__(kFiThreads, 4) fiberip_kernel(const __grid_constant__ FiberIpArgs<N> a) {
+__global__ void __launch_bounds__(fi_max_threads<D>(), fi_min_blocks<D>())
+fiberip_kernel(const __grid_constant__ FiberIpArgs<N> a, int G) {
     constexpr int NN = N * N, NX = D == 3 ? NN * N : NN;
     constexpr int NF = NX / N;   // fibers per instance and stage
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
     uint64_t* empty = full + kFiMaxRing;
-    float* ring = reinterpret_cast<float*>(smem + 128);
+    float* ring = reinterpret_cast<float*>(smem + 256);
     const int NB = a.nstage, P = a.P;
     const int tile_words = P * NX;
-    const int tid = threadIdx.x;
+    const int ncompute = kFiCompute * G;
+    const int gidx = threadIdx.x / kFiCompute;
+    const int tid = threadIdx.x - kFiCompute * gidx;   // thread within its compute group
     const int64_t ntiles = (a.batch + P - 1) / P;
     const int64_t grid = gridDim.x;
-    if (tid == 0) {
+    if (threadIdx.x == 0) {
         for (int s = 0; s < NB; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], kFiCompute);
@@ -91,8 +100,8 @@ __global__ void __launch_bounds__(kFiThreads, 4) fiberip_kernel(const __grid_con
     }
     __syncthreads();
 
-    if (tid >= kFiCompute) {   // producer
-        const int lane = tid - kFiCompute;
+    if (threadIdx.x >= ncompute) {   // producer
+        const int lane = threadIdx.x - ncompute;
         const uint64_t pol = l2_evict_first_policy();
         float* Y = static_cast<float*>(a.Y);
         const float* X = static_cast<const float*>(a.X);
@@ -135,8 +144,8 @@ __global__ void __launch_bounds__(kFiThreads, 4) fiberip_kernel(const __grid_con
 
     const float* X = static_cast<const float*>(a.X);
     float* Y = static_cast<float*>(a.Y);
-    int it = 0;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += grid, ++it) {
+    for (int it = gidx; blockIdx.x + (int64_t)it * grid < ntiles; it += G) {
+        const int64_t tile = blockIdx.x + (int64_t)it * grid;
         const int s = it % NB;
         float* buf = ring + s * tile_words;
         const int64_t i0 = tile * P;
@@ -145,7 +154,7 @@ __global__ void __launch_bounds__(kFiThreads, 4) fiberip_kernel(const __grid_con
         const bool ok = mbar_wait_bounded(&full[s], (unsigned)(it / NB) & 1u, a.err);
         if (nbulk != nel) {   // ragged last tile: the elements past the last 16-byte chunk
             for (int e = nbulk + tid; e < nel; e += kFiCompute) buf[e] = X[i0 * NX + e];
-            compute_sync_or(false);
+            group_sync_or(false, gidx);
         }
         if constexpr (D == 3) {
             // Stage A (mode 3): fibers (q, i, j), consecutive threads consecutive i.
@@ -155,7 +164,7 @@ __global__ void __launch_bounds__(kFiThreads, 4) fiberip_kernel(const __grid_con
                 fiber_in_place<N, NN>(buf + q * NX + r, a.m3);
             }
         }
-        if (compute_sync_or(!ok)) {
+        if (group_sync_or(!ok, gidx)) {
             if (tid == 0)
                 for (int j = it; j < it + NB; ++j)
                     if (blockIdx.x + (int64_t)j * grid < ntiles)
@@ -169,7 +178,7 @@ __global__ void __launch_bounds__(kFiThreads, 4) fiberip_kernel(const __grid_con
             const int i = r % N, k = r / N;
             fiber_in_place<N, N>(buf + q * NX + i + NN * k, a.m2);
         }
-        compute_sync_or(false);
+        group_sync_or(false, gidx);
         // Stage C (mode 1): fibers (q, j, k) (contiguous), with the epilogue.
 #pragma unroll 1
         for (int u = tid; u < cnt * NF; u += kFiCompute) {
@@ -190,7 +199,7 @@ __global__ void __launch_bounds__(kFiThreads, 4) fiberip_kernel(const __grid_con
             }
         }
         if (nbulk != nel) {   // ragged last tile: the tail the bulk copy leaves out
-            compute_sync_or(false);
+            group_sync_or(false, gidx);
             for (int e = nbulk + tid; e < nel; e += kFiCompute) Y[i0 * NX + e] = buf[e];
         }
         fence_proxy_async_smem();
@@ -233,11 +242,19 @@ kron_status launch_fi_n(const KronDesc& d, cudaStream_t st) {
     a.err = device_error_word();
     if (!a.err) return KRON_ERR_CUDA;
     a.P = d.P > 0 ? d.P : P0;
-    int nb = d.nstage >= 1 ? d.nstage : 2;   // measured: two buffers at every odd n
+    // compute warps: 2-D four groups of four (one CTA per SM), 3-D one group
+    const int W = d.warps > 0 ? d.warps : (D == 2 ? 16 : 4);
+    const int G = W / 4;
+    if (W % 4 || G < 1 || G > (D == 2 ? kFiMaxGroups : 1)) return KRON_ERR_NOT_SUPPORTED;
+    // ring depth: measured two buffers per group; a multiple of the group count, so
+    // that buffer it % NB passes from a group to itself (a parity wait cannot tell
+    // phase u from phase u - 2)
+    int nb = d.nstage >= 1 ? d.nstage : 2 * G;
     if (nb > kFiMaxRing) nb = kFiMaxRing;
-    auto smem_of = [&](int n_b) { return 128 + (size_t)n_b * a.P * NX * sizeof(float); };
+    nb = nb < G ? G : nb / G * G;
+    auto smem_of = [&](int n_b) { return 256 + (size_t)n_b * a.P * NX * sizeof(float); };
     size_t smem = smem_of(nb);
-    while (nb > 1 && smem > dev.smem_per_block_optin) smem = smem_of(--nb);
+    while (nb > G && smem > dev.smem_per_block_optin) smem = smem_of(nb -= G);
     if (smem > dev.smem_per_block_optin) return KRON_ERR_NOT_SUPPORTED;
     a.nstage = nb;
     auto kern = fiberip_kernel<N, D>;
@@ -246,12 +263,12 @@ kron_status launch_fi_n(const KronDesc& d, cudaStream_t st) {
     int64_t grid = d.grid;
     if (grid <= 0) {
         int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kFiThreads, smem) != cudaSuccess)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kFiCompute * G + 32, smem) != cudaSuccess)
             return KRON_ERR_CUDA;
         grid = (int64_t)(per_sm < 1 ? 1 : per_sm) * dev.sms;
     }
     grid = std::max<int64_t>(1, std::min<int64_t>(grid, ntiles));
-    kern<<<(unsigned)grid, kFiThreads, smem, st>>>(a);
+    kern<<<(unsigned)grid, kFiCompute * G + 32, smem, st>>>(a, G);
     return cudaPeekAtLastError() == cudaSuccess ? KRON_OK : KRON_ERR_CUDA;
 }
 

@@ -108,7 +108,7 @@ bool warps_ok(int kind, int n, kron_dtype io, kron_compute comp, int variant, in
     if (warps == 0) return true;
     if (kind == 3 && comp == KRON_COMPUTE_32F_BF16X3)   // warps sharing one instance
         return warps == 1 || warps == 2 || warps == 4 || warps == 8;
-    if (kind == 2 && (n == 10 || n == 14) && io == KRON_R32F && comp == KRON_COMPUTE_NATIVE &&
+    if (kind == 2 && (n == 10 || n == 14 || ((n & 1) && n >= 3)) && io == KRON_R32F && comp == KRON_COMPUTE_NATIVE &&
         (variant == KRON_VARIANT_AUTO || variant == KRON_VARIANT_IN_PLACE))   // groups of four warps
         return warps % 4 == 0 && warps <= 16;
     if (kind != 2 || n != 16 || io != KRON_R32F || comp != KRON_COMPUTE_NATIVE) return false;

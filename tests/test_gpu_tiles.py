@@ -126,16 +126,19 @@ def test_autotune_config_then_correct(kind, n, io):
     check(Y, b, X64, io)
 
 
-# The FP32 2-D n = 10, 14 in-place body: one to four compute groups of four warps
+# The FP32 2-D in-place bodies for n = 10, 14 and odd n: one to four compute groups of four warps
 # sharing a CTA's ring, tiles of multiples of 8 instances, several ring depths;
 # every configuration gives the same bits (the same arithmetic per instance).
-@pytest.mark.parametrize("n", [10, 14])
+@pytest.mark.parametrize("n", [10, 14, 15, 7])
 @pytest.mark.parametrize("batch", [5, 1001])
 def test_in_place_groups_same_bits(n, batch):
     b = inputs.make_batch(2, n, batch, seed=600 + n + batch, x_dist="normal")
     outs = []
     try:
-        for P, depth, warps in [(48, 1, 4), (48, 10, 16), (40, 5, 16), (16, 6, 12), (8, 3, 8), (24, 12, 16)]:
+        shapes = [(48, 1, 4), (48, 10, 16), (40, 5, 16), (16, 6, 12), (8, 3, 8), (24, 12, 16)]
+        if n % 2:   # odd n: tiles of a multiple of 4 instances
+            shapes = [(24, 2, 4), (24, 8, 16), (12, 6, 12), (4, 3, 8), (8, 12, 16), (44, 1, 16)]
+        for P, depth, warps in shapes:
             kg.set_kernel_config(2, n, "f32", "native", "in_place", P, depth, 0, warps)
             Y, X64 = run_gpu(b, io="f32", guard=8)
             outs.append(Y)
