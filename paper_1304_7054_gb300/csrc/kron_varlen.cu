@@ -793,7 +793,18 @@ KRON_API kron_status kron_varlen_tune(kron_varlen_plan* plan, const void* X, voi
         const int pmax = vl_max_P(kind, n, elem_size(plan->io), kVlMaxBufBytes);
         const int cur = plan->P[key];
         int best_P = cur;
-        for (int cand : {cur / 2, cur * 2, cur * 4, cur / 4, cur + cur / 2}) {
+        // Besides the neighbours of the current tile: the tile whose fibers per stage
+        // fill the CTA's threads most evenly (P n^(kind-1) against whole rounds of
+        // kVlThreads), the smallest such when several tie.
+        const int fib = kind == 2 ? n : n * n;
+        int even_P = 1;
+        double even_eff = 0.0;
+        for (int q = 1; q <= pmax; ++q) {
+            const int rounds = (q * fib + kVlThreads - 1) / kVlThreads;
+            const double eff = (double)(q * fib) / ((double)rounds * kVlThreads);
+            if (eff > even_eff + 1e-9) { even_eff = eff; even_P = q; }
+        }
+        for (int cand : {cur / 2, cur * 2, cur * 4, cur / 4, cur + cur / 2, even_P}) {
             if (cand < 1 || cand > pmax || cand == cur) continue;
             plan->P[key] = cand;
             vl_build(plan);
