@@ -361,8 +361,8 @@ KRON_API kron_status kron_autotune_config(kron_stream_t stream, int kind, int n,
  * column-major, host pointers, 'N' op; C only for kind 3).  A plan may hold at
  * most one class per (kind, n).  Instance p belongs to class h_class_of[p];
  * its operand starts at element offset h_x_off[p] of X and its result at
- * h_y_off[p] of Y; instances are contiguous (minimal leading dimensions),
- * alpha = 1, beta = 0.  Storage: KRON_R32F or KRON_R16BF / KRON_R16F
+ * h_y_off[p] of Y; instances are contiguous (minimal leading dimensions);
+ * alpha and beta are 1 and 0 unless kron_varlen_plan_set_scaling sets them.  Storage: KRON_R32F or KRON_R16BF / KRON_R16F
  * (components float).  X and Y may span at most 2^31 - 1 elements each
  * (KRON_ERR_NOT_SUPPORTED beyond).  X and Y need only element alignment, and
  * the offsets are arbitrary: the kernel copies the 16-byte-aligned span around
@@ -406,6 +406,15 @@ KRON_API kron_status kron_varlen_execute(kron_varlen_plan* plan, const void* X, 
 KRON_API kron_status kron_varlen_tune(kron_varlen_plan* plan, const void* X, void* Y,
                                       void* workspace, size_t workspace_bytes,
                                       kron_stream_t stream);
+/*
+ * kron_varlen_plan_set_scaling -- alpha and beta of the plan's later executes:
+ * Y^p = alpha (K_c X^p) + beta Y^p for every instance (Sec. 2.2's alpha and beta,
+ * shared by the whole batch; default alpha = 1, beta = 0).  With beta = 0, Y is
+ * not read (NaN or Inf in it are overwritten).  With beta != 0 the outputs must
+ * not overlap one another.  alpha and beta enter the kernel as FP32.  Errors:
+ * KRON_ERR_INVALID_VALUE for a null plan or a non-finite alpha or beta.
+ */
+KRON_API kron_status kron_varlen_plan_set_scaling(kron_varlen_plan* plan, double alpha, double beta);
 KRON_API kron_status kron_varlen_plan_destroy(kron_varlen_plan* plan);
 
 /*

@@ -54,6 +54,7 @@ SIGNATURES = {
     "kron_varlen_execute": ([_P, _P, _P, _P, _S, _P], _I),
     "kron_varlen_tune": ([_P, _P, _P, _P, _S, _P], _I),
     "kron_varlen_plan_destroy": ([_P], _I),
+    "kron_varlen_plan_set_scaling": ([_P, ctypes.c_double, ctypes.c_double], _I),
     "kron_varlen_execute_noalloc": ([_P, _P, _P, _P], _I),
 }
 
@@ -426,6 +427,11 @@ class VarlenPlan:
         _check(load_library().kron_varlen_execute_noalloc(self.handle, xp, yp, _stream_handle(stream)),
                "kron_varlen_execute_noalloc")
         return Y
+
+    def set_scaling(self, alpha=1.0, beta=0.0):
+        """alpha and beta of later executes: Y = alpha (K X) + beta Y per instance."""
+        _check(load_library().kron_varlen_plan_set_scaling(self.handle, float(alpha), float(beta)),
+               "kron_varlen_plan_set_scaling")
 
     def tune(self, X, Y, workspace, stream=None):
         xp, yp = self._operands(X, Y)

@@ -33,6 +33,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <mutex>
 #include <vector>
 
@@ -79,6 +80,8 @@ struct __align__(8) VarlenArgs {
     const void* X;
     void* Y;
     int ntiles;
+    int alpha_one, beta_zero;  // Y = alpha (K x) + beta Y (beta = 0: Y is not read)
+    float alpha, beta;
     unsigned* err;
 };
 
@@ -196,11 +199,26 @@ __device__ __forceinline__ void vl_store_pairs(float* dst, const f2 (&y)[vl_rows
     for (int r = 0; r < vl_rows(N) / 2; ++r) *reinterpret_cast<f2*>(dst + 2 * r) = y[r];
 }
 
-// Output fiber of N elements at dst[0..N) (contiguous): pairs (rows 2r, 2r+1)
-// rounded to the storage type and stored as one word where dst is aligned for
-// it, else element by element (the padding row of an odd N is dropped).
+// Output fiber of N elements at dst[0..N) (contiguous): the epilogue alpha y +
+// beta yold (yold: the same N elements of Y in global memory, read only when
+// beta != 0), then pairs (rows 2r, 2r+1) rounded to the storage type and stored
+// as one word where dst is aligned for it, else element by element (the padding
+// row of an odd N is dropped).
 template <typename S, int N>
-__device__ __forceinline__ void vl_stage_out(S* dst, const f2 (&y)[vl_rows(N) / 2]) {
+__device__ __forceinline__ void vl_stage_out(S* dst, f2 (&y)[vl_rows(N) / 2], const VarlenArgs& a, const S* yold) {
+    if (!a.alpha_one) {
+        const f2 al = f2_pack(a.alpha, a.alpha);
+#pragma unroll
+        for (int r = 0; r < vl_rows(N) / 2; ++r) y[r] = fmul2(y[r], al);
+    }
+    if (!a.beta_zero) {
+#pragma unroll
+        for (int r = 0; r < vl_rows(N) / 2; ++r) {
+            const float o0 = load_cvt<float, S>(yold[2 * r]);
+            const float o1 = 2 * r + 1 < N ? load_cvt<float, S>(yold[2 * r + 1]) : 0.f;
+            y[r] = f2_pack(__fmaf_rn(a.beta, o0, f2_lo(y[r])), __fmaf_rn(a.beta, o1, f2_hi(y[r])));
+        }
+    }
     const bool paired = ((uintptr_t)dst & (2 * sizeof(S) - 1)) == 0;
     if (paired) {
 #pragma unroll
@@ -263,7 +281,8 @@ __device__ __forceinline__ void vl_tile(const VarlenArgs& a, int4 td, unsigned c
             for (int l = 0; l < N; ++l) w[l] = wr[KP * l];
             f2 y[R];
             vl_contract<N>(m1, w, y);
-            vl_stage_out<S, N>(reinterpret_cast<S*>(xt + q * SLOT) + vl_phase<S>(Y, yo[q]) + N * j, y);
+            vl_stage_out<S, N>(reinterpret_cast<S*>(xt + q * SLOT) + vl_phase<S>(Y, yo[q]) + N * j, y, a,
+                               static_cast<const S*>(Y) + yo[q] + N * j);
         }
     } else {
         const int F = cnt * N * N;
@@ -300,7 +319,8 @@ __device__ __forceinline__ void vl_tile(const VarlenArgs& a, int4 td, unsigned c
             for (int l = 0; l < N; ++l) u[l] = ur[KP * N * l];
             f2 y[R];
             vl_contract<N>(m1, u, y);
-            vl_stage_out<S, N>(reinterpret_cast<S*>(ex1 + q * EXQ) + vl_phase<S>(Y, yo[q]) + N * (j + N * k), y);
+            vl_stage_out<S, N>(reinterpret_cast<S*>(ex1 + q * EXQ) + vl_phase<S>(Y, yo[q]) + N * (j + N * k), y, a,
+                               static_cast<const S*>(Y) + yo[q] + N * (j + N * k));
         }
     }
 }
@@ -475,6 +495,7 @@ struct kron_varlen_plan {
     int version = 0;                           // bumped whenever the tables change
     int graph_version = -1;                    // tables the instantiated graph was built for
     int device = -1;
+    double alpha = 1.0, beta = 0.0;            // kron_varlen_plan_set_scaling
 };
 
 namespace kron {
@@ -540,6 +561,10 @@ static kron_status vl_fill_args(kron_varlen_plan* p, const void* X, void* Y, voi
     a.X = X;
     a.Y = Y;
     a.ntiles = (int)p->tiles.size();
+    a.alpha = (float)p->alpha;
+    a.beta = (float)p->beta;
+    a.alpha_one = p->alpha == 1.0;
+    a.beta_zero = p->beta == 0.0;
     a.err = device_error_word();
     return a.err ? KRON_OK : KRON_ERR_CUDA;
 }
@@ -882,6 +907,13 @@ KRON_API kron_status kron_varlen_execute_noalloc(kron_varlen_plan* plan, const v
     void* kargs[2] = {plan->args, &xbe};
     if (cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(kVlThreads), kargs, plan->smem, st) != cudaSuccess)
         return KRON_ERR_CUDA;
+    return KRON_OK;
+}
+
+KRON_API kron_status kron_varlen_plan_set_scaling(kron_varlen_plan* plan, double alpha, double beta) {
+    if (!plan || !std::isfinite(alpha) || !std::isfinite(beta)) return KRON_ERR_INVALID_VALUE;
+    plan->alpha = alpha;   // read by the next execute (the kernel node's parameters are set on every call)
+    plan->beta = beta;
     return KRON_OK;
 }
 

@@ -224,3 +224,54 @@ def test_varlen_unaligned_bases_and_permuted_output(io):
     e = max_err(v, Yh, reference(v, X64), io, y_off=y_off)
     assert e <= bar(io), e
     plan.close()
+
+
+@pytest.mark.parametrize("io", ["f32", "bf16"])
+def test_varlen_alpha_beta(io):
+    """Y = alpha (K X) + beta Y per instance (kron_varlen_plan_set_scaling), against
+    the oracle with the same alpha, beta and starting Y; back to the plain action
+    after alpha = 1, beta = 0."""
+    import torch
+    v = inputs.make_varlen(1500, seed=14, nmin=1, nmax=16)
+    al, be = 0.75, -1.5
+    rng = np.random.default_rng(9)
+    Y0 = rng.standard_normal(v.total).astype(np.float32)
+    if io == "f32":
+        Yd, Y064 = torch.from_numpy(Y0.copy()).cuda(), Y0.astype(np.float64)
+        X, X64 = torch.from_numpy(v.X).cuda(), v.X.astype(np.float64)
+    else:
+        t0 = inputs.to_storage(Y0, io)
+        Yd, Y064 = t0.cuda(), inputs.storage_to_f64(t0)
+        t = inputs.to_storage(v.X, io)
+        X, X64 = t.cuda(), inputs.storage_to_f64(t)
+    plan = kg.VarlenPlan(classes_of(v), v.class_of, v.x_off, v.y_off, io=io)
+    ws = plan.alloc_workspace()
+    plan.set_scaling(al, be)
+    plan.execute(X, Yd, ws)
+    torch.cuda.synchronize()
+    assert kg.device_status() == 0
+    got = Yd.double().cpu().numpy()
+    ref, norm, absref = reference(v, X64)
+    worst = 0.0
+    for p, r in ref.items():
+        kind, n = v.classes[v.class_of[p]]
+        nx = n ** kind
+        y0 = Y064[v.y_off[p]:v.y_off[p] + nx]
+        want = al * r + be * y0
+        g = got[v.y_off[p]:v.y_off[p] + nx]
+        if io == "f32":
+            scale = abs(al) * norm[p] + abs(be) * np.abs(y0).max() + 1e-300
+            worst = max(worst, np.abs(g - want).max() / scale)
+        else:
+            worst = max(worst, storage_excess(g, want, abs(al) * absref[p], io, arith_factor(kind, n),
+                                              abs(be) * np.abs(y0)))
+    assert worst <= (2 * TOL["f32"] if io == "f32" else 1.0), worst
+    # alpha = 1, beta = 0 again: the plain action on the same plan and graph
+    plan.set_scaling(1.0, 0.0)
+    Yn = torch.full((v.total,), float("nan"), dtype=torch_dtype(io), device="cuda")
+    plan.execute(X, Yn, ws)
+    torch.cuda.synchronize()
+    assert max_err(v, Yn.double().cpu().numpy(), (ref, norm, absref), io) <= bar(io)
+    with pytest.raises(kg.KronError):
+        plan.set_scaling(float("nan"), 0.0)
+    plan.close()
