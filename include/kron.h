@@ -411,7 +411,9 @@ KRON_API kron_status kron_varlen_tune(kron_varlen_plan* plan, const void* X, voi
  * Y^p = alpha (K_c X^p) + beta Y^p for every instance (Sec. 2.2's alpha and beta,
  * shared by the whole batch; default alpha = 1, beta = 0).  With beta = 0, Y is
  * not read (NaN or Inf in it are overwritten).  With beta != 0 the outputs must
- * not overlap one another.  alpha and beta enter the kernel as FP32.  Errors:
+ * not overlap one another.  alpha and beta enter the kernel as FP32; the scaling
+ * is a pass over the staged results, so with 16-bit storage K_c X^p is rounded to
+ * the storage type before it is scaled (two roundings).  Errors:
  * KRON_ERR_INVALID_VALUE for a null plan or a non-finite alpha or beta.
  */
 KRON_API kron_status kron_varlen_plan_set_scaling(kron_varlen_plan* plan, double alpha, double beta);

@@ -199,26 +199,11 @@ __device__ __forceinline__ void vl_store_pairs(float* dst, const f2 (&y)[vl_rows
     for (int r = 0; r < vl_rows(N) / 2; ++r) *reinterpret_cast<f2*>(dst + 2 * r) = y[r];
 }
 
-// Output fiber of N elements at dst[0..N) (contiguous): the epilogue alpha y +
-// beta yold (yold: the same N elements of Y in global memory, read only when
-// beta != 0), then pairs (rows 2r, 2r+1) rounded to the storage type and stored
-// as one word where dst is aligned for it, else element by element (the padding
-// row of an odd N is dropped).
+// Output fiber of N elements at dst[0..N) (contiguous): pairs (rows 2r, 2r+1)
+// rounded to the storage type and stored as one word where dst is aligned for
+// it, else element by element (the padding row of an odd N is dropped).
 template <typename S, int N>
-__device__ __forceinline__ void vl_stage_out(S* dst, f2 (&y)[vl_rows(N) / 2], const VarlenArgs& a, const S* yold) {
-    if (!a.alpha_one) {
-        const f2 al = f2_pack(a.alpha, a.alpha);
-#pragma unroll
-        for (int r = 0; r < vl_rows(N) / 2; ++r) y[r] = fmul2(y[r], al);
-    }
-    if (!a.beta_zero) {
-#pragma unroll
-        for (int r = 0; r < vl_rows(N) / 2; ++r) {
-            const float o0 = load_cvt<float, S>(yold[2 * r]);
-            const float o1 = 2 * r + 1 < N ? load_cvt<float, S>(yold[2 * r + 1]) : 0.f;
-            y[r] = f2_pack(__fmaf_rn(a.beta, o0, f2_lo(y[r])), __fmaf_rn(a.beta, o1, f2_hi(y[r])));
-        }
-    }
+__device__ __forceinline__ void vl_stage_out(S* dst, const f2 (&y)[vl_rows(N) / 2]) {
     const bool paired = ((uintptr_t)dst & (2 * sizeof(S) - 1)) == 0;
     if (paired) {
 #pragma unroll
@@ -281,8 +266,7 @@ __device__ __forceinline__ void vl_tile(const VarlenArgs& a, int4 td, unsigned c
             for (int l = 0; l < N; ++l) w[l] = wr[KP * l];
             f2 y[R];
             vl_contract<N>(m1, w, y);
-            vl_stage_out<S, N>(reinterpret_cast<S*>(xt + q * SLOT) + vl_phase<S>(Y, yo[q]) + N * j, y, a,
-                               static_cast<const S*>(Y) + yo[q] + N * j);
+            vl_stage_out<S, N>(reinterpret_cast<S*>(xt + q * SLOT) + vl_phase<S>(Y, yo[q]) + N * j, y);
         }
     } else {
         const int F = cnt * N * N;
@@ -319,8 +303,7 @@ __device__ __forceinline__ void vl_tile(const VarlenArgs& a, int4 td, unsigned c
             for (int l = 0; l < N; ++l) u[l] = ur[KP * N * l];
             f2 y[R];
             vl_contract<N>(m1, u, y);
-            vl_stage_out<S, N>(reinterpret_cast<S*>(ex1 + q * EXQ) + vl_phase<S>(Y, yo[q]) + N * (j + N * k), y, a,
-                               static_cast<const S*>(Y) + yo[q] + N * (j + N * k));
+            vl_stage_out<S, N>(reinterpret_cast<S*>(ex1 + q * EXQ) + vl_phase<S>(Y, yo[q]) + N * (j + N * k), y);
         }
     }
 }
@@ -349,7 +332,7 @@ __device__ __forceinline__ void vl_dispatch_n(const VarlenArgs& a, int4 td, unsi
 }
 
 template <typename S>
-__global__ void __launch_bounds__(kVlThreads) varlen_kernel(const __grid_constant__ VarlenArgs a, int xbuf_bytes) {
+__global__ void __launch_bounds__(kVlThreads, 3) varlen_kernel(const __grid_constant__ VarlenArgs a, int xbuf_bytes) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);   // one barrier per operand buffer
     // Offsets of the instances of three consecutive tiles of this CTA (a ring):
@@ -425,6 +408,24 @@ __global__ void __launch_bounds__(kVlThreads) varlen_kernel(const __grid_constan
             vl_dispatch_n<S, 2>(a, d0, xt, ex1, xo, yo);
         else
             vl_dispatch_n<S, 3>(a, d0, xt, ex1, xo, yo);
+        if (!a.alpha_one || !a.beta_zero) {
+            // Epilogue Y = alpha (K x) + beta Y on the staged results (a separate pass,
+            // so the contraction bodies stay as small as without it).  The values are
+            // the storage-rounded results: for 16-bit storage this rounds twice.
+            __syncthreads();
+            const int nx = vl_nx(key);
+            const int slot = key < 16 ? vl_xs_bytes(2, n, (int)sizeof(S)) : 4 * vl_e1_floats(3, n, (int)sizeof(S));
+            unsigned char* base = key < 16 ? xt : reinterpret_cast<unsigned char*>(ex1);
+            const S* Yg = static_cast<const S*>(a.Y);
+            for (int e = tid; e < d0.z * nx; e += kVlThreads) {
+                const int q = e / nx, r = e - q * nx;
+                S* v = reinterpret_cast<S*>(base + q * slot) + vl_phase<S>(a.Y, yo[q]) + r;
+                float o = load_cvt<float, S>(*v);
+                if (!a.alpha_one) o *= a.alpha;
+                if (!a.beta_zero) o = __fmaf_rn(a.beta, load_cvt<float, S>(Yg[yo[q] + r]), o);
+                *v = store_cvt<S, float>(o);
+            }
+        }
         fence_proxy_async_smem();   // results visible to the bulk copies
         __syncthreads();
         if (tid < 32) {
