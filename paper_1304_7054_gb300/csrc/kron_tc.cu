@@ -725,7 +725,7 @@ __global__ void __launch_bounds__(256) tc3g_kernel(const __grid_constant__ TcArg
         const uint32_t tb_s = smem_u32(tb);
 
         // ---- modes 1 and 2: plane pairs 2w, 2w + 2W, ... ---------------------------------
-#pragma unroll 1
+#pragma unroll 2
         for (int p = 2 * warp; p < N; p += 2 * W) {
             const bool two = p + 1 < N;
             unsigned bh0[4], bl0[4], bh1[4], bl1[4];
@@ -744,7 +744,7 @@ __global__ void __launch_bounds__(256) tc3g_kernel(const __grid_constant__ TcArg
 
         // ---- mode 3: row-block pairs 2w, 2w + 2W, ... -------------------------------------
         S* yq = static_cast<S*>(a.Y) + inst * NX;
-#pragma unroll 1
+#pragma unroll 2
         for (int mt = 2 * warp; mt < N; mt += 2 * W) {
             tc3_rows<S, N>(a, yq, tb_s, mt, lane, m3h, m3l);
             if (mt + 1 < N) tc3_rows<S, N>(a, yq, tb_s, mt + 1, lane, m3h, m3l);
