@@ -243,3 +243,9 @@ def test_kernel_config_validation_and_round_trip(lib):
     assert lib.kron_set_kernel_config(3, 12, f32, 0, ctypes.byref(cfg(0, 0, 0, 0))) == 0
     assert lib.kron_get_kernel_config(3, 12, f32, 0, ctypes.byref(got)) == 0
     assert (got.variant, got.instances_per_tile, got.pipeline_depth, got.fibers_per_step) == (0, 0, 0, 0)
+
+
+def test_varlen_set_scaling_validation(lib):
+    """kron_varlen_plan_set_scaling validates before touching the plan (no GPU needed)."""
+    assert lib.kron_varlen_plan_set_scaling(None, 1.0, 0.0) == INVALID
+    assert lib.kron_varlen_plan_set_scaling(None, float("nan"), 0.0) == INVALID
