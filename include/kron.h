@@ -313,15 +313,25 @@ KRON_API kron_status kron_autotune(kron_stream_t stream, int kind, int n, int64_
  *                       next instance's operand arriving meanwhile.
  *
  * kron_set_kernel_config returns KRON_ERR_NOT_SUPPORTED when the body does not
- * exist for (kind, n, io, comp) (in place: 2-D n = 16 any storage -- FP32 with
+ * exist for (kind, n, io, comp) (CUDA-core bodies, KRON_COMPUTE_NATIVE -- in
+ * place: 2-D n = 16 any storage -- FP32 with
  * tiles of 8, 16, 24 or 32 instances, 16-bit with 16 --, FP32 2-D n =
  * 10, 14, FP32 3-D n = 10, 14, 16, FP32 odd n; exchange: even n, FP32 or 16-bit
- * storage; scalar: every real storage type) and KRON_ERR_INVALID_VALUE for
+ * storage; scalar: every real storage type; the split tensor bodies below)
+ * and KRON_ERR_INVALID_VALUE for
  * values out of range; all-zero restores the built-in default.  Strided,
- * transposed or misaligned batches always run the scalar body.  The split
- * tensor path (KRON_COMPUTE_32F_BF16X3) and complex storage have one body each:
- * only instances_per_tile and pipeline_depth apply there (and compute_warps
- * for the 3-D tensor body).
+ * transposed or misaligned batches always run the scalar body.  The 2-D split
+ * tensor path (KRON_COMPUTE_32F_BF16X3, FP32 or 16-bit storage) has two bodies:
+ * KRON_VARIANT_IN_PLACE, one zero-padded 16 x 16 tile per instance (n <= 8:
+ * several instances on the tile's diagonal), the second product taking the
+ * first's accumulators; and KRON_VARIANT_EXCHANGE (9 <= n <= 16), 8 / gcd(n, 8)
+ * instances side by side along the MMA's N dimension with the intermediate
+ * passed through per-warp exchange rows in shared memory, so that only the
+ * contracted dimension and the component rows are padded.  The built-in
+ * choice is the stacked body for n = 10 and 12 (and FP32 at n = 14) and the
+ * padded one otherwise; both give the same bits.  The 3-D split tensor path and complex storage have one body
+ * each: only instances_per_tile and pipeline_depth apply there (and
+ * compute_warps for the 3-D tensor body).
  *
  * kron_autotune_config times every configuration of that space on the
  * caller's buffers (as kron_autotune; Y is overwritten), keeps the fastest

@@ -47,6 +47,11 @@ __device__ __forceinline__ void mma_f16_16816(float (&d)[4], const unsigned (&a)
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+// mma.sync.aligned and ldmatrix.sync.aligned need the whole warp converged on the
+// same instruction; the groups of them that follow bounds tests or tail stores
+// (which may leave the lanes diverged) start with a warp synchronisation.
+__device__ __forceinline__ void converge() { __syncwarp(); }
+
 // (x0, x1) -> packed bf16 pairs hi = (bf16(x0), bf16(x1)), lo = (bf16(x0 - hi0), bf16(x1 - hi1)).
 __device__ __forceinline__ void split_pair(float x0, float x1, unsigned& hi, unsigned& lo) {
     asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(hi) : "f"(x1), "f"(x0));
@@ -72,6 +77,7 @@ struct TcArgs2 {
     int P;
     int nstage;
     int beta_zero, alpha_one;
+    int ypair;                  // Y aligned to two elements: the stacked body stores pairs
     float alpha, beta;
     unsigned* err;
 };
@@ -129,26 +135,18 @@ __device__ __forceinline__ void tc2_instance(const TcArgs2<N>& a, const S* const
                                              const unsigned (&f1l)[4]) {
     const int lane = threadIdx.x & 31;
     const int g = lane >> 2, t = lane & 3;
-    // ---- stage 1: W = M1 X ---------------------------------------------------------------
-    float w[2][4];
+    if constexpr (sizeof(S) == 4) {
+        // FP32 storage: one n-tile after the other (measured faster than the
+        // step-by-step order below, which pays off for 16-bit storage).
+        // ---- stage 1: W = M1 X -----------------------------------------------------------
+        float w[2][4];
 #pragma unroll
-    for (int nt = 0; nt < 2; ++nt) {
-        const int m = 8 * nt + g;
+        for (int nt = 0; nt < 2; ++nt) {
+            const int m = 8 * nt + g;
 #pragma unroll
-        for (int e = 0; e < 4; ++e) w[nt][e] = 0.f;
-        if constexpr (sizeof(S) == 2 && std::is_same<S, __nv_bfloat16>::value) {
-            const unsigned b0 = x_pair_bf16_blk<N, B>(xq, 2 * t, m);
-            const unsigned b1 = x_pair_bf16_blk<N, B>(xq, 2 * t + 8, m);
-            mma_bf16_16816(w[nt], m1l, b0, b1);
-            mma_bf16_16816(w[nt], m1h, b0, b1);
-        } else if (std::is_same<S, __half>::value && a.f16a) {
-            const unsigned b0 = x_pair_bf16_blk<N, B>(xq, 2 * t, m);
-            const unsigned b1 = x_pair_bf16_blk<N, B>(xq, 2 * t + 8, m);
-            mma_f16_16816(w[nt], f1l, b0, b1);
-            mma_f16_16816(w[nt], f1h, b0, b1);
-        } else {
+            for (int e = 0; e < 4; ++e) w[nt][e] = 0.f;
             float x0, x1, x2, x3;
-            if constexpr (N == 16 && sizeof(S) == 4) {
+            if constexpr (N == 16) {
                 const float2 p0 = *reinterpret_cast<const float2*>(xq[0] + 2 * t + 16 * m);
                 const float2 p1 = *reinterpret_cast<const float2*>(xq[0] + 2 * t + 8 + 16 * m);
                 x0 = p0.x; x1 = p0.y; x2 = p1.x; x3 = p1.y;
@@ -159,36 +157,120 @@ __device__ __forceinline__ void tc2_instance(const TcArgs2<N>& a, const S* const
             unsigned bh0, bl0, bh1, bl1;
             split_pair(x0, x1, bh0, bl0);
             split_pair(x2, x3, bh1, bl1);
+            converge();
             mma_bf16_16816(w[nt], m1l, bh0, bh1);
             mma_bf16_16816(w[nt], m1h, bl0, bl1);
             mma_bf16_16816(w[nt], m1h, bh0, bh1);
         }
-    }
-    // ---- stage 2: Y = W M2^T, W from the accumulators ------------------------------------
-    unsigned wh[4], wl[4];
-    split_pair(w[0][0], w[0][1], wh[0], wl[0]);
-    split_pair(w[0][2], w[0][3], wh[1], wl[1]);
-    split_pair(w[1][0], w[1][1], wh[2], wl[2]);
-    split_pair(w[1][2], w[1][3], wh[3], wl[3]);
+        // ---- stage 2: Y = W M2^T, W from the accumulators --------------------------------
+        unsigned wh[4], wl[4];
+        split_pair(w[0][0], w[0][1], wh[0], wl[0]);
+        split_pair(w[0][2], w[0][3], wh[1], wl[1]);
+        split_pair(w[1][0], w[1][1], wh[2], wl[2]);
+        split_pair(w[1][2], w[1][3], wh[3], wl[3]);
 #pragma unroll
-    for (int nt = 0; nt < 2; ++nt) {
-        float y[4] = {0.f, 0.f, 0.f, 0.f};
-        mma_bf16_16816(y, wl, m2h[nt][0], m2h[nt][1]);
-        mma_bf16_16816(y, wh, m2l[nt][0], m2l[nt][1]);
-        mma_bf16_16816(y, wh, m2h[nt][0], m2h[nt][1]);
-        const int j = 8 * nt + 2 * t;
+        for (int nt = 0; nt < 2; ++nt) {
+            float y[4] = {0.f, 0.f, 0.f, 0.f};
+            converge();
+            mma_bf16_16816(y, wl, m2h[nt][0], m2h[nt][1]);
+            mma_bf16_16816(y, wh, m2l[nt][0], m2l[nt][1]);
+            mma_bf16_16816(y, wh, m2h[nt][0], m2h[nt][1]);
+            const int j = 8 * nt + 2 * t;
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int i = g + 8 * (e >> 1), jj = j + (e & 1);
-            const int b = i / B, il = i % B, jl = jj % B;
-            if (b == jj / B && yq[b] && il < N && jl < N) {
-                S* dst = yq[b] + il + N * jl;
-                float v = a.alpha_one ? y[e] : a.alpha * y[e];
-                if (!a.beta_zero) v = fmaf(a.beta, load_cvt<float, S>(*dst), v);
-                if constexpr (sizeof(S) == 4)
+            for (int e = 0; e < 4; ++e) {
+                const int i = g + 8 * (e >> 1), jj = j + (e & 1);
+                const int b = i / B, il = i % B, jl = jj % B;
+                if (b == jj / B && yq[b] && il < N && jl < N) {
+                    S* dst = yq[b] + il + N * jl;
+                    float v = a.alpha_one ? y[e] : a.alpha * y[e];
+                    if (!a.beta_zero) v = fmaf(a.beta, load_cvt<float, S>(*dst), v);
                     __stcs(reinterpret_cast<float*>(dst), v);
-                else
+                }
+            }
+        }
+    } else {
+        // ---- stage 1: W = M1 X ---------------------------------------------------------------
+        // The MMAs go step by step across the two n-tiles (the first products of both,
+        // then the second ...): one n-tile's dependent products are separated by the other's.
+        float w[2][4];
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) w[nt][e] = 0.f;
+        if constexpr (std::is_same<S, __nv_bfloat16>::value) {
+            unsigned b0[2], b1[2];
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) {
+                b0[nt] = x_pair_bf16_blk<N, B>(xq, 2 * t, 8 * nt + g);
+                b1[nt] = x_pair_bf16_blk<N, B>(xq, 2 * t + 8, 8 * nt + g);
+            }
+            converge();
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) mma_bf16_16816(w[nt], m1l, b0[nt], b1[nt]);
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) mma_bf16_16816(w[nt], m1h, b0[nt], b1[nt]);
+        } else if (std::is_same<S, __half>::value && a.f16a) {
+            unsigned b0[2], b1[2];
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) {
+                b0[nt] = x_pair_bf16_blk<N, B>(xq, 2 * t, 8 * nt + g);
+                b1[nt] = x_pair_bf16_blk<N, B>(xq, 2 * t + 8, 8 * nt + g);
+            }
+            converge();
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) mma_f16_16816(w[nt], f1l, b0[nt], b1[nt]);
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) mma_f16_16816(w[nt], f1h, b0[nt], b1[nt]);
+        } else {
+            unsigned bh0[2], bl0[2], bh1[2], bl1[2];
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) {
+                const int m = 8 * nt + g;   // f16 storage without the scaled f16 split
+                float x0, x1, x2, x3;
+                x_pair_blk<S, N, B>(xq, 2 * t, m, x0, x1);
+                x_pair_blk<S, N, B>(xq, 2 * t + 8, m, x2, x3);
+                split_pair(x0, x1, bh0[nt], bl0[nt]);
+                split_pair(x2, x3, bh1[nt], bl1[nt]);
+            }
+            converge();
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) mma_bf16_16816(w[nt], m1l, bh0[nt], bh1[nt]);
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) mma_bf16_16816(w[nt], m1h, bl0[nt], bl1[nt]);
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) mma_bf16_16816(w[nt], m1h, bh0[nt], bh1[nt]);
+        }
+        // ---- stage 2: Y = W M2^T, W from the accumulators ------------------------------------
+        unsigned wh[4], wl[4];
+        split_pair(w[0][0], w[0][1], wh[0], wl[0]);
+        split_pair(w[0][2], w[0][3], wh[1], wl[1]);
+        split_pair(w[1][0], w[1][1], wh[2], wl[2]);
+        split_pair(w[1][2], w[1][3], wh[3], wl[3]);
+        float y[2][4];
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) y[nt][e] = 0.f;
+        converge();
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) mma_bf16_16816(y[nt], wl, m2h[nt][0], m2h[nt][1]);
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) mma_bf16_16816(y[nt], wh, m2l[nt][0], m2l[nt][1]);
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) mma_bf16_16816(y[nt], wh, m2h[nt][0], m2h[nt][1]);
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+            const int j = 8 * nt + 2 * t;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int i = g + 8 * (e >> 1), jj = j + (e & 1);
+                const int b = i / B, il = i % B, jl = jj % B;
+                if (b == jj / B && yq[b] && il < N && jl < N) {
+                    S* dst = yq[b] + il + N * jl;
+                    float v = a.alpha_one ? y[nt][e] : a.alpha * y[nt][e];
+                    if (!a.beta_zero) v = fmaf(a.beta, load_cvt<float, S>(*dst), v);
                     *dst = store_cvt<S, float>(v);
+                }
             }
         }
     }
@@ -383,6 +465,7 @@ __device__ __forceinline__ void tc3_plane_load(const S* xs, int p, int g, int t,
         // 8 nt .. 8 nt + 7), so lane (g, t) receives X_p[8 nt + g][8 h + 2t, +1].
         const int lane = 4 * g + t, mi = lane >> 3, r = lane & 7;
         unsigned v[4];
+        converge();
         ldsm_x4_trans(v, smem_u32(xs + 8 * (mi >> 1) + 16 * (8 * (mi & 1) + r) + 256 * p));
         if constexpr (std::is_same<S, __nv_bfloat16>::value) {
 #pragma unroll
@@ -439,6 +522,7 @@ __device__ __forceinline__ void tc3_plane_compute(const unsigned (&bh)[4], const
                                                   float (&z)[2][4], bool f16a, const unsigned (&f2h)[4],
                                                   const unsigned (&f2l)[4]) {
     float w[2][4];
+    converge();
 #pragma unroll
     for (int nt = 0; nt < 2; ++nt) {
 #pragma unroll
@@ -467,6 +551,74 @@ __device__ __forceinline__ void tc3_plane_compute(const unsigned (&bh)[4], const
     }
 }
 
+// Planes p and p + 1 at once: the same products in the same order per output as
+// two tc3_plane_compute calls, issued step by step across the four (plane,
+// n-tile) chains so that the dependent MMAs of one chain are separated by the
+// independent ones of the other three.
+template <bool XEXACT>
+__device__ __forceinline__ void tc3_planes_compute2(const unsigned (&bh0)[4], const unsigned (&bl0)[4],
+                                                    const unsigned (&bh1)[4], const unsigned (&bl1)[4],
+                                                    const unsigned (&m2h)[4], const unsigned (&m2l)[4],
+                                                    const unsigned (&m1h)[2][2], const unsigned (&m1l)[2][2],
+                                                    float (&z0)[2][4], float (&z1)[2][4], bool f16a,
+                                                    const unsigned (&f2h)[4], const unsigned (&f2l)[4]) {
+    float w0[2][4], w1[2][4];
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) w0[nt][e] = w1[nt][e] = 0.f;
+    if (f16a) {   // f16 products plane by plane (step by step measured 2-6x slower with several warps)
+        tc3_plane_compute<XEXACT>(bh0, bl0, m2h, m2l, m1h, m1l, z0, f16a, f2h, f2l);
+        tc3_plane_compute<XEXACT>(bh1, bl1, m2h, m2l, m1h, m1l, z1, f16a, f2h, f2l);
+        return;
+    }
+    converge();
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) {
+        mma_bf16_16816(w0[nt], m2l, bh0[2 * nt], bh0[2 * nt + 1]);
+        mma_bf16_16816(w1[nt], m2l, bh1[2 * nt], bh1[2 * nt + 1]);
+    }
+    if constexpr (!XEXACT) {
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+            mma_bf16_16816(w0[nt], m2h, bl0[2 * nt], bl0[2 * nt + 1]);
+            mma_bf16_16816(w1[nt], m2h, bl1[2 * nt], bl1[2 * nt + 1]);
+        }
+    }
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) {
+        mma_bf16_16816(w0[nt], m2h, bh0[2 * nt], bh0[2 * nt + 1]);
+        mma_bf16_16816(w1[nt], m2h, bh1[2 * nt], bh1[2 * nt + 1]);
+    }
+    unsigned wh0[4], wl0[4], wh1[4], wl1[4];
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) {
+        split_pair(w0[nt][0], w0[nt][1], wh0[2 * nt], wl0[2 * nt]);
+        split_pair(w0[nt][2], w0[nt][3], wh0[2 * nt + 1], wl0[2 * nt + 1]);
+        split_pair(w1[nt][0], w1[nt][1], wh1[2 * nt], wl1[2 * nt]);
+        split_pair(w1[nt][2], w1[nt][3], wh1[2 * nt + 1], wl1[2 * nt + 1]);
+    }
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) z0[nt][e] = z1[nt][e] = 0.f;
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) {
+        mma_bf16_16816(z0[nt], wl0, m1h[nt][0], m1h[nt][1]);
+        mma_bf16_16816(z1[nt], wl1, m1h[nt][0], m1h[nt][1]);
+    }
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) {
+        mma_bf16_16816(z0[nt], wh0, m1l[nt][0], m1l[nt][1]);
+        mma_bf16_16816(z1[nt], wh1, m1l[nt][0], m1l[nt][1]);
+    }
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) {
+        mma_bf16_16816(z0[nt], wh0, m1h[nt][0], m1h[nt][1]);
+        mma_bf16_16816(z1[nt], wh1, m1h[nt][0], m1h[nt][1]);
+    }
+}
+
 // z[nt] = T^T[j' = g, g+8][i = 8 nt + 2t, +1] of plane p -> row p of T, r = i + 16 j'.
 __device__ __forceinline__ void tc3_plane_store(unsigned char* tb, int p, int g, int t, const float (&z)[2][4]) {
 #pragma unroll
@@ -483,52 +635,104 @@ __device__ __forceinline__ void tc3_plane_store(unsigned char* tb, int p, int g,
     }
 }
 
+// Results y of row block mt, n-tile nt: Y[i][mt][k] for i = g, g + 8 and
+// k = 8 nt + 2t, +1, with the epilogue.
+template <typename S, int N>
+__device__ __forceinline__ void tc3_store(const TcArgs3<N>& a, S* yq, int mt, int nt, int g, int t,
+                                          const float (&y)[4]) {
+    if constexpr (N == 16 && sizeof(S) == 2) {
+        if (a.beta_zero && a.ypair) {
+            // Pairs of adjacent rows i (lanes g, g ^ 1) as one 32-bit store:
+            // the even lane stores column k = 2t, the odd lane k = 2t + 1.
+            float v[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) v[e] = a.alpha_one ? y[e] : a.alpha * y[e];
+            const bool odd = g & 1;
+            const float s1 = __shfl_xor_sync(0xffffffffu, odd ? v[0] : v[1], 4);
+            const float s3 = __shfl_xor_sync(0xffffffffu, odd ? v[2] : v[3], 4);
+            const int i0 = g & ~1, k = 8 * nt + 2 * t + (odd ? 1 : 0);
+            const f2 lo = odd ? f2_pack(s1, v[1]) : f2_pack(v[0], s1);
+            const f2 hi = odd ? f2_pack(s3, v[3]) : f2_pack(v[2], s3);
+            *reinterpret_cast<unsigned*>(yq + i0 + N * mt + N * N * k) = pack16<S>(lo);
+            *reinterpret_cast<unsigned*>(yq + i0 + 8 + N * mt + N * N * k) = pack16<S>(hi);
+            return;
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int i = g + 8 * (e >> 1), k = 8 * nt + 2 * t + (e & 1);
+        if (i < N && k < N) {
+            S* dst = yq + i + N * mt + N * N * k;
+            float v = a.alpha_one ? y[e] : a.alpha * y[e];
+            if (!a.beta_zero) v = fmaf(a.beta, load_cvt<float, S>(*dst), v);
+            if constexpr (sizeof(S) == 4)
+                __stcs(reinterpret_cast<float*>(dst), v);
+            else
+                *dst = store_cvt<S, float>(v);
+        }
+    }
+}
+
 template <typename S, int N>
 __device__ __forceinline__ void tc3_rows(const TcArgs3<N>& a, S* yq, uint32_t tb_s, int mt, int lane,
                                          const unsigned (&m3h)[2][2], const unsigned (&m3l)[2][2]) {
     const int g = lane >> 2, t = lane & 3, mi = lane >> 3, rr = lane & 7;
     unsigned ah[4], al[4];
     const uint32_t to = trow_off(rr + 8 * (mi >> 1), 2 * mt + (mi & 1));
+    converge();
     ldsm_x4_trans(ah, tb_s + to);
     ldsm_x4_trans(al, tb_s + to + 512);
+    float y[2][4];
 #pragma unroll
     for (int nt = 0; nt < 2; ++nt) {
-        float y[4] = {0.f, 0.f, 0.f, 0.f};
-        mma_bf16_16816(y, al, m3h[nt][0], m3h[nt][1]);
-        mma_bf16_16816(y, ah, m3l[nt][0], m3l[nt][1]);
-        mma_bf16_16816(y, ah, m3h[nt][0], m3h[nt][1]);
-        if constexpr (N == 16 && sizeof(S) == 2) {
-            if (a.beta_zero && a.ypair) {
-                // Pairs of adjacent rows i (lanes g, g ^ 1) as one 32-bit store:
-                // the even lane stores column k = 2t, the odd lane k = 2t + 1.
-                float v[4];
 #pragma unroll
-                for (int e = 0; e < 4; ++e) v[e] = a.alpha_one ? y[e] : a.alpha * y[e];
-                const bool odd = g & 1;
-                const float s1 = __shfl_xor_sync(0xffffffffu, odd ? v[0] : v[1], 4);
-                const float s3 = __shfl_xor_sync(0xffffffffu, odd ? v[2] : v[3], 4);
-                const int i0 = g & ~1, k = 8 * nt + 2 * t + (odd ? 1 : 0);
-                const f2 lo = odd ? f2_pack(s1, v[1]) : f2_pack(v[0], s1);
-                const f2 hi = odd ? f2_pack(s3, v[3]) : f2_pack(v[2], s3);
-                *reinterpret_cast<unsigned*>(yq + i0 + N * mt + N * N * k) = pack16<S>(lo);
-                *reinterpret_cast<unsigned*>(yq + i0 + 8 + N * mt + N * N * k) = pack16<S>(hi);
-                continue;
-            }
-        }
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int i = g + 8 * (e >> 1), k = 8 * nt + 2 * t + (e & 1);
-            if (i < N && k < N) {
-                S* dst = yq + i + N * mt + N * N * k;
-                float v = a.alpha_one ? y[e] : a.alpha * y[e];
-                if (!a.beta_zero) v = fmaf(a.beta, load_cvt<float, S>(*dst), v);
-                if constexpr (sizeof(S) == 4)
-                    __stcs(reinterpret_cast<float*>(dst), v);
-                else
-                    *dst = store_cvt<S, float>(v);
-            }
-        }
+        for (int e = 0; e < 4; ++e) y[nt][e] = 0.f;
+        mma_bf16_16816(y[nt], al, m3h[nt][0], m3h[nt][1]);
+        mma_bf16_16816(y[nt], ah, m3l[nt][0], m3l[nt][1]);
+        mma_bf16_16816(y[nt], ah, m3h[nt][0], m3h[nt][1]);
     }
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) tc3_store<S, N>(a, yq, mt, nt, g, t, y[nt]);
+}
+
+// Row blocks mt and mt + 1 at once, step by step across the four (row block,
+// n-tile) chains (the same products in the same order per output).
+template <typename S, int N>
+__device__ __forceinline__ void tc3_rows2(const TcArgs3<N>& a, S* yq, uint32_t tb_s, int mt, int lane,
+                                          const unsigned (&m3h)[2][2], const unsigned (&m3l)[2][2]) {
+    const int g = lane >> 2, t = lane & 3, mi = lane >> 3, rr = lane & 7;
+    unsigned ah0[4], al0[4], ah1[4], al1[4];
+    const uint32_t to0 = trow_off(rr + 8 * (mi >> 1), 2 * mt + (mi & 1));
+    const uint32_t to1 = trow_off(rr + 8 * (mi >> 1), 2 * (mt + 1) + (mi & 1));
+    converge();
+    ldsm_x4_trans(ah0, tb_s + to0);
+    ldsm_x4_trans(al0, tb_s + to0 + 512);
+    ldsm_x4_trans(ah1, tb_s + to1);
+    ldsm_x4_trans(al1, tb_s + to1 + 512);
+    float y0[2][4], y1[2][4];
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) y0[nt][e] = y1[nt][e] = 0.f;
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) {
+        mma_bf16_16816(y0[nt], al0, m3h[nt][0], m3h[nt][1]);
+        mma_bf16_16816(y1[nt], al1, m3h[nt][0], m3h[nt][1]);
+    }
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) {
+        mma_bf16_16816(y0[nt], ah0, m3l[nt][0], m3l[nt][1]);
+        mma_bf16_16816(y1[nt], ah1, m3l[nt][0], m3l[nt][1]);
+    }
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) {
+        mma_bf16_16816(y0[nt], ah0, m3h[nt][0], m3h[nt][1]);
+        mma_bf16_16816(y1[nt], ah1, m3h[nt][0], m3h[nt][1]);
+    }
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) tc3_store<S, N>(a, yq, mt, nt, g, t, y0[nt]);
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) tc3_store<S, N>(a, yq, mt + 1, nt, g, t, y1[nt]);
 }
 
 template <typename S, int N>
@@ -610,8 +814,12 @@ __global__ void __launch_bounds__(32 * kTc3Warps) tc3_kernel(const __grid_consta
             tc3_plane_load<S, N>(xq, p, g, t, bh0, bl0, f16a);
             if (two) tc3_plane_load<S, N>(xq, p + 1, g, t, bh1, bl1, f16a);
             float z0[2][4], z1[2][4];
-            tc3_plane_compute<XEXACT>(bh0, bl0, m2h, m2l, m1h, m1l, z0, f16a, f2h, f2l);
-            if (two) tc3_plane_compute<XEXACT>(bh1, bl1, m2h, m2l, m1h, m1l, z1, f16a, f2h, f2l);
+            if constexpr (N % 2 == 0) {   // planes come in pairs: both at once
+                tc3_planes_compute2<XEXACT>(bh0, bl0, bh1, bl1, m2h, m2l, m1h, m1l, z0, z1, f16a, f2h, f2l);
+            } else {
+                tc3_plane_compute<XEXACT>(bh0, bl0, m2h, m2l, m1h, m1l, z0, f16a, f2h, f2l);
+                if (two) tc3_plane_compute<XEXACT>(bh1, bl1, m2h, m2l, m1h, m1l, z1, f16a, f2h, f2l);
+            }
             __syncwarp();   // planes p, p+1 are read by every lane before they are overwritten
             tc3_plane_store(tb, p, g, t, z0);
             if (two) tc3_plane_store(tb, p + 1, g, t, z1);
@@ -632,8 +840,12 @@ __global__ void __launch_bounds__(32 * kTc3Warps) tc3_kernel(const __grid_consta
         S* yq = static_cast<S*>(a.Y) + inst * NX;
 #pragma unroll 1
         for (int mt = 0; mt < N; mt += 2) {
-            tc3_rows<S, N>(a, yq, tb_s, mt, lane, m3h, m3l);
-            if (mt + 1 < N) tc3_rows<S, N>(a, yq, tb_s, mt + 1, lane, m3h, m3l);
+            if constexpr (N % 2 == 0) {   // row blocks come in pairs: both at once
+                tc3_rows2<S, N>(a, yq, tb_s, mt, lane, m3h, m3l);
+            } else {
+                tc3_rows<S, N>(a, yq, tb_s, mt, lane, m3h, m3l);
+                if (mt + 1 < N) tc3_rows<S, N>(a, yq, tb_s, mt + 1, lane, m3h, m3l);
+            }
         }
         __syncwarp();   // T is free (in place: so are the operand planes)
         if constexpr (L::INPLACE) fetch_next();
@@ -732,8 +944,12 @@ __global__ void __launch_bounds__(256) tc3g_kernel(const __grid_constant__ TcArg
             tc3_plane_load<S, N>(xq, p, g, t, bh0, bl0, f16a);
             if (two) tc3_plane_load<S, N>(xq, p + 1, g, t, bh1, bl1, f16a);
             float z0[2][4], z1[2][4];
-            tc3_plane_compute<XEXACT>(bh0, bl0, m2h, m2l, m1h, m1l, z0, f16a, f2h, f2l);
-            if (two) tc3_plane_compute<XEXACT>(bh1, bl1, m2h, m2l, m1h, m1l, z1, f16a, f2h, f2l);
+            if constexpr (N % 2 == 0) {   // planes come in pairs: both at once
+                tc3_planes_compute2<XEXACT>(bh0, bl0, bh1, bl1, m2h, m2l, m1h, m1l, z0, z1, f16a, f2h, f2l);
+            } else {
+                tc3_plane_compute<XEXACT>(bh0, bl0, m2h, m2l, m1h, m1l, z0, f16a, f2h, f2l);
+                if (two) tc3_plane_compute<XEXACT>(bh1, bl1, m2h, m2l, m1h, m1l, z1, f16a, f2h, f2l);
+            }
             __syncwarp();   // planes p, p+1 are read by every lane before they are overwritten
             tc3_plane_store(tb, p, g, t, z0);
             if (two) tc3_plane_store(tb, p + 1, g, t, z1);
@@ -746,12 +962,410 @@ __global__ void __launch_bounds__(256) tc3g_kernel(const __grid_constant__ TcArg
         S* yq = static_cast<S*>(a.Y) + inst * NX;
 #pragma unroll 2
         for (int mt = 2 * warp; mt < N; mt += 2 * W) {
-            tc3_rows<S, N>(a, yq, tb_s, mt, lane, m3h, m3l);
-            if (mt + 1 < N) tc3_rows<S, N>(a, yq, tb_s, mt + 1, lane, m3h, m3l);
+            if constexpr (N % 2 == 0) {   // row blocks come in pairs: both at once
+                tc3_rows2<S, N>(a, yq, tb_s, mt, lane, m3h, m3l);
+            } else {
+                tc3_rows<S, N>(a, yq, tb_s, mt, lane, m3h, m3l);
+                if (mt + 1 < N) tc3_rows<S, N>(a, yq, tb_s, mt + 1, lane, m3h, m3l);
+            }
         }
         fence_proxy_async_smem();
         __syncthreads();            // T free (in place: so is the operand buffer)
         if (L::INPLACE && threadIdx.x == 0 && inst + 2 * G < a.batch) fetch(b, inst + 2 * G);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 2-D, 9 <= n <= 16: instances stacked along the MMA's N dimension (tc2s_kernel).
+//
+// The padded tile spends 16^3 of MMA work per product on an instance's n^3.
+// Stacking G = 8 / gcd(n, 8) instances side by side makes G n a whole number of
+// 8-wide n-tiles, so only the contracted dimension and the component's rows
+// stay padded to 16 (bf16 storage at n = 12: 7.5 MMAs per instance instead of
+// 10; n = 10: 6.25).
+//   stage 1  W = M1 [X_1 ... X_G]   A = M1 (constant), B = the instances'
+//            columns side by side: n-tile column 8 nt + g = q n + c is column c
+//            of instance q.  W is split and written to the warp's exchange
+//            buffer, row rho = q n + r holding W_q[r][0 .. n-1] (hi, then lo).
+//   stage 2  Y_q^T = M2 W_q^T       A = M2 (constant), B = exchange rows read by
+//            ldmatrix, stacked along N as rho.  Accumulator lane (g, t) holds
+//            Y_q[r][j] and Y_q[r + 1][j] (rho = 8 nt + 2 t, j = g and g + 8):
+//            adjacent in column-major Y, one paired store for even n.
+// The exchange rows' columns n .. 15 stay zero (the padding of the stage-2
+// contraction).  Rows are 80 bytes apart, so the eight rows of one ldmatrix
+// matrix fall in eight distinct 16-byte bank groups.
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int tc2s_group(int n) {
+    return n % 8 == 0 ? 1 : (n % 4 == 0 ? 2 : (n % 2 == 0 ? 4 : 8));
+}
+constexpr int kTc2sRow = 80;   // exchange row: 16 hi + 16 lo 16-bit values, 16 bytes of padding
+
+__device__ __forceinline__ void ldsm_x4(unsigned (&r)[4], uint32_t addr) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr)
+                 : "memory");
+}
+
+// A fragment (m16k16, row-major) of a 16 x 16 component stored as packed pairs.
+__device__ __forceinline__ void a_frag(const unsigned* m, int g, int t, unsigned (&f)[4]) {
+    f[0] = m[g * 8 + t];
+    f[1] = m[(g + 8) * 8 + t];
+    f[2] = m[g * 8 + t + 4];
+    f[3] = m[(g + 8) * 8 + t + 4];
+}
+
+// W[r][cc], W[r][cc + 1] (stacked columns) into the exchange rows, split.
+template <int N>
+__device__ __forceinline__ void tc2s_put(unsigned char* ex, int cc, int r, float v0, float v1) {
+    unsigned hi, lo;
+    split_pair(v0, v1, hi, lo);
+    const int q0 = cc / N, c0 = cc - q0 * N;
+    unsigned char* p0 = ex + (q0 * N + r) * kTc2sRow + 2 * c0;
+    if constexpr (N % 2 == 0) {   // c0 even: both columns in one instance, 4-byte aligned
+        *reinterpret_cast<unsigned*>(p0) = hi;
+        *reinterpret_cast<unsigned*>(p0 + 32) = lo;
+    } else {                      // the second column may open the next instance
+        const int q1 = (cc + 1) / N, c1 = cc + 1 - q1 * N;
+        unsigned char* p1 = ex + (q1 * N + r) * kTc2sRow + 2 * c1;
+        *reinterpret_cast<unsigned short*>(p0) = (unsigned short)hi;
+        *reinterpret_cast<unsigned short*>(p0 + 32) = (unsigned short)lo;
+        *reinterpret_cast<unsigned short*>(p1) = (unsigned short)(hi >> 16);
+        *reinterpret_cast<unsigned short*>(p1 + 32) = (unsigned short)(lo >> 16);
+    }
+}
+
+// One result element Y_q[r][j] (stacked row rho = q n + r) with the epilogue.
+template <typename S, int N>
+__device__ __forceinline__ void tc2s_out1(const TcArgs2<N>& a, S* yg, int live, int rho, int j, float v) {
+    const int q = rho / N, r = rho - q * N;
+    if (q >= live) return;
+    S* dst = yg + q * N * N + r + N * j;
+    if (!a.alpha_one) v *= a.alpha;
+    if (!a.beta_zero) v = fmaf(a.beta, load_cvt<float, S>(*dst), v);
+    if constexpr (sizeof(S) == 4)
+        __stcs(reinterpret_cast<float*>(dst), v);
+    else
+        *dst = store_cvt<S, float>(v);
+}
+
+// Y_q[r][j], Y_q[r + 1][j] (rho = q n + r even).
+template <typename S, int N>
+__device__ __forceinline__ void tc2s_out(const TcArgs2<N>& a, S* yg, int live, int rho, int j, float v0, float v1) {
+    if constexpr (N % 2 == 0) {
+        const int q = rho / N, r = rho - q * N;
+        if (q >= live) return;
+        S* dst = yg + q * N * N + r + N * j;
+        if (a.ypair) {
+            if (!a.alpha_one) {
+                v0 *= a.alpha;
+                v1 *= a.alpha;
+            }
+            if (!a.beta_zero) {
+                v0 = fmaf(a.beta, load_cvt<float, S>(dst[0]), v0);
+                v1 = fmaf(a.beta, load_cvt<float, S>(dst[1]), v1);
+            }
+            if constexpr (sizeof(S) == 4)
+                __stcs(reinterpret_cast<float2*>(dst), make_float2(v0, v1));
+            else
+                __stcs(reinterpret_cast<unsigned*>(dst), pack16<S>(f2_pack(v0, v1)));
+            return;
+        }
+    }
+    tc2s_out1<S, N>(a, yg, live, rho, j, v0);
+    tc2s_out1<S, N>(a, yg, live, rho + 1, j, v1);
+}
+
+// Constant A fragments of the stacked body: M1 (stage 1; f16 storage: M1 2^s as
+// an f16 split) and M2 (stage 2).
+struct Tc2sFrags {
+    unsigned m1h[4], m1l[4], f1h[4], f1l[4], m2h[4], m2l[4];
+};
+
+// One group of G instances, any n, any epilogue, any number of live instances.
+template <typename S, int N>
+__device__ __forceinline__ void tc2s_group_any(const TcArgs2<N>& a, const Tc2sFrags& f, const S* xg, S* yg, int live,
+                                               unsigned char* ex, uint32_t ex_s) {
+    constexpr int NX = N * N, G = tc2s_group(N), NT = G * N / 8;
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    // ---- stage 1: W = M1 [X_1 ... X_G] ---------------------------------------------------
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) {
+        const int col = 8 * nt + g, q = col / N, c = col - q * N;
+        const bool lq = q < live;
+        const S* xq = xg + q * NX;
+        float w[4] = {0.f, 0.f, 0.f, 0.f};
+        if constexpr (std::is_same<S, __nv_bfloat16>::value) {
+            const unsigned b0 = lq ? x_pair_bf16<N>(xq, 2 * t, c) : 0u;
+            const unsigned b1 = lq ? x_pair_bf16<N>(xq, 2 * t + 8, c) : 0u;
+            converge();
+            mma_bf16_16816(w, f.m1l, b0, b1);
+            mma_bf16_16816(w, f.m1h, b0, b1);
+        } else if (std::is_same<S, __half>::value && a.f16a) {
+            const unsigned b0 = lq ? x_pair_bf16<N>(xq, 2 * t, c) : 0u;
+            const unsigned b1 = lq ? x_pair_bf16<N>(xq, 2 * t + 8, c) : 0u;
+            converge();
+            mma_f16_16816(w, f.f1l, b0, b1);
+            mma_f16_16816(w, f.f1h, b0, b1);
+        } else {
+            float x0 = 0.f, x1 = 0.f, x2 = 0.f, x3 = 0.f;
+            if (lq) {
+                x_pair<S, N>(xq, 2 * t, c, x0, x1);
+                x_pair<S, N>(xq, 2 * t + 8, c, x2, x3);
+            }
+            unsigned bh0, bl0, bh1, bl1;
+            split_pair(x0, x1, bh0, bl0);
+            split_pair(x2, x3, bh1, bl1);
+            converge();
+            mma_bf16_16816(w, f.m1l, bh0, bh1);
+            mma_bf16_16816(w, f.m1h, bl0, bl1);
+            mma_bf16_16816(w, f.m1h, bh0, bh1);
+        }
+        // lane holds W[g][cc], W[g][cc + 1], W[g + 8][cc], W[g + 8][cc + 1]
+        const int cc = 8 * nt + 2 * t;
+        tc2s_put<N>(ex, cc, g, w[0], w[1]);
+        if (g + 8 < N) tc2s_put<N>(ex, cc, g + 8, w[2], w[3]);
+    }
+    __syncwarp();
+    // ---- stage 2: Y_q^T = M2 W_q^T, stacked --------------------------------------------------
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) {
+        unsigned b[4];   // hi (k 0-7, k 8-15), lo (k 0-7, k 8-15)
+        converge();
+        ldsm_x4(b, ex_s + (8 * nt + (lane & 7)) * kTc2sRow + (lane >> 3) * 16);
+        float y[4] = {0.f, 0.f, 0.f, 0.f};   // products in the padded body's order
+        mma_bf16_16816(y, f.m2h, b[2], b[3]);
+        mma_bf16_16816(y, f.m2l, b[0], b[1]);
+        mma_bf16_16816(y, f.m2h, b[0], b[1]);
+        const int rho = 8 * nt + 2 * t;
+        tc2s_out<S, N>(a, yg, live, rho, g, y[0], y[1]);
+        if (g + 8 < N) tc2s_out<S, N>(a, yg, live, rho, g + 8, y[2], y[3]);
+    }
+    __syncwarp();
+}
+
+// The lane's offsets in the fast path (even n): per n-tile, the element offset of
+// its X pair (column c of instance q, rows 2t, 2t + 1), the byte offset of its
+// exchange store (row q n + g, columns 2t, 2t + 1 of the stacked W), the element
+// offset of its Y pair (rows r, r + 1 of instance q', column g), and q' (the
+// instance its stores belong to, for the last, partial group).
+template <int N>
+struct Tc2sLane {
+    static constexpr int NT = tc2s_group(N) * N / 8;
+    int xo[NT], eo[NT], yo[NT], qy[NT];
+};
+
+template <int N>
+__device__ __forceinline__ void tc2s_lane_init(Tc2sLane<N>& L, int g, int t) {
+#pragma unroll
+    for (int nt = 0; nt < Tc2sLane<N>::NT; ++nt) {
+        const int col = 8 * nt + g, q = col / N, c = col - q * N;
+        L.xo[nt] = q * N * N + N * c + 2 * t;
+        const int rho = 8 * nt + 2 * t, q2 = rho / N, r = rho - q2 * N;
+        L.eo[nt] = (q2 * N + g) * kTc2sRow + 2 * r;
+        L.yo[nt] = q2 * N * N + r + N * g;
+        L.qy[nt] = q2;
+    }
+}
+
+// A group of an even n with the plain epilogue (alpha = 1, beta = 0, Y aligned to
+// pairs): offsets from the lane's table, and the MMAs issued step by step across
+// the n-tiles (every n-tile's first product, then every second, ...), so that the
+// dependent products of one n-tile are separated by the independent ones of the
+// others.  In the last, partial group the operand slots of absent instances
+// (q >= live) are read as they are -- stale values of the ring or the exchange
+// rows after it, inside the CTA's shared memory (at most G - 1 instances past a
+// tile) -- and only their stores are skipped: every column of W and every
+// stacked row of the result depends on its own instance alone.
+template <typename S, int N>
+__device__ __forceinline__ void tc2s_group_fast(const Tc2sFrags& f, const Tc2sLane<N>& L, const S* xg, S* yg,
+                                                int live, unsigned char* ex, uint32_t ex_s) {
+    constexpr int NT = Tc2sLane<N>::NT;
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const bool k8 = 2 * t + 8 < N;   // the lane's rows 2t + 8, 2t + 9 exist
+    const bool r8 = g + 8 < N;       // the lane's W row / Y column g + 8 exists
+    // ---- stage 1 ----------------------------------------------------------------------------
+    float w[NT][4];
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) w[nt][e] = 0.f;
+    if constexpr (sizeof(S) == 2) {
+        unsigned b0[NT], b1[NT];
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+            const unsigned* xp = reinterpret_cast<const unsigned*>(xg + L.xo[nt]);
+            b0[nt] = xp[0];
+            b1[nt] = k8 ? xp[4] : 0u;
+        }
+        if constexpr (std::is_same<S, __half>::value) {
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) mma_f16_16816(w[nt], f.f1l, b0[nt], b1[nt]);
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) mma_f16_16816(w[nt], f.f1h, b0[nt], b1[nt]);
+        } else {
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) mma_bf16_16816(w[nt], f.m1l, b0[nt], b1[nt]);
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) mma_bf16_16816(w[nt], f.m1h, b0[nt], b1[nt]);
+        }
+    } else {
+        unsigned bh0[NT], bl0[NT], bh1[NT], bl1[NT];
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+            const float2 p0 = *reinterpret_cast<const float2*>(xg + L.xo[nt]);
+            const float2 p1 = k8 ? *reinterpret_cast<const float2*>(xg + L.xo[nt] + 8) : make_float2(0.f, 0.f);
+            split_pair(p0.x, p0.y, bh0[nt], bl0[nt]);
+            split_pair(p1.x, p1.y, bh1[nt], bl1[nt]);
+        }
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) mma_bf16_16816(w[nt], f.m1l, bh0[nt], bh1[nt]);
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) mma_bf16_16816(w[nt], f.m1h, bl0[nt], bl1[nt]);
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) mma_bf16_16816(w[nt], f.m1h, bh0[nt], bh1[nt]);
+    }
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) {
+        unsigned hi, lo;
+        split_pair(w[nt][0], w[nt][1], hi, lo);
+        *reinterpret_cast<unsigned*>(ex + L.eo[nt]) = hi;
+        *reinterpret_cast<unsigned*>(ex + L.eo[nt] + 32) = lo;
+        if (r8) {
+            split_pair(w[nt][2], w[nt][3], hi, lo);
+            *reinterpret_cast<unsigned*>(ex + L.eo[nt] + 8 * kTc2sRow) = hi;
+            *reinterpret_cast<unsigned*>(ex + L.eo[nt] + 8 * kTc2sRow + 32) = lo;
+        }
+    }
+    __syncwarp();
+    // ---- stage 2 ----------------------------------------------------------------------------
+    const uint32_t lrow = ex_s + (lane & 7) * kTc2sRow + (lane >> 3) * 16;
+    unsigned b[NT][4];
+    float y[NT][4];
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) {
+        ldsm_x4(b[nt], lrow + nt * 8 * kTc2sRow);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) y[nt][e] = 0.f;
+    }
+    __syncwarp();   // exchange rows read: the next group may overwrite them
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) mma_bf16_16816(y[nt], f.m2h, b[nt][2], b[nt][3]);
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) mma_bf16_16816(y[nt], f.m2l, b[nt][0], b[nt][1]);
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) mma_bf16_16816(y[nt], f.m2h, b[nt][0], b[nt][1]);
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) {
+        if (L.qy[nt] >= live) continue;
+        S* dst = yg + L.yo[nt];
+        if constexpr (sizeof(S) == 4) {
+            __stcs(reinterpret_cast<float2*>(dst), make_float2(y[nt][0], y[nt][1]));
+            if (r8) __stcs(reinterpret_cast<float2*>(dst + 8 * N), make_float2(y[nt][2], y[nt][3]));
+        } else {
+            __stcs(reinterpret_cast<unsigned*>(dst), pack16<S>(f2_pack(y[nt][0], y[nt][1])));
+            if (r8) __stcs(reinterpret_cast<unsigned*>(dst + 8 * N), pack16<S>(f2_pack(y[nt][2], y[nt][3])));
+        }
+    }
+}
+
+// FAST: every group by tc2s_group_fast (even n, plain epilogue, the stored operand
+// entering the MMAs as it is or split from FP32); else by tc2s_group_any.  The two
+// bodies are separate kernels: one kernel never chooses between them at run time.
+template <typename S, int N, bool FAST>
+__global__ void __launch_bounds__(kTcThreads) tc2s_kernel(const __grid_constant__ TcArgs2<N> a) {
+    constexpr int NX = N * N, G = tc2s_group(N);
+    static_assert(N >= 9 && N <= 16 && (G * N) % 8 == 0, "stacked body: 9 <= n <= 16");
+    static_assert(!FAST || N % 2 == 0, "the fast body takes even n");
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+    const int P = a.P;
+    const size_t xstage = round_up((size_t)P * NX * sizeof(S), 128);
+    unsigned char* xbase = smem + 128;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int g = lane >> 2, t = lane & 3;
+    const int64_t ntiles = (a.batch + P - 1) / P;
+    const int64_t grid = gridDim.x;
+    unsigned char* ex = xbase + a.nstage * xstage + warp * (G * N * kTc2sRow);
+    const uint32_t ex_s = (uint32_t)__cvta_generic_to_shared(ex);
+    for (int e = lane; e < G * N * kTc2sRow / 4; e += 32) reinterpret_cast<unsigned*>(ex)[e] = 0u;
+
+    Tc2sFrags f;
+    for (int e = 0; e < 4; ++e) f.f1h[e] = f.f1l[e] = 0u;
+    if (std::is_same<S, __half>::value && a.f16a) {
+        a_frag(a.f1h, g, t, f.f1h);
+        a_frag(a.f1l, g, t, f.f1l);
+    }
+    a_frag(a.m1h, g, t, f.m1h);
+    a_frag(a.m1l, g, t, f.m1l);
+    a_frag(a.m2h, g, t, f.m2h);
+    a_frag(a.m2l, g, t, f.m2l);
+    Tc2sLane<N> L;
+    if constexpr (FAST) tc2s_lane_init<N>(L, g, t);
+
+    uint64_t pol = 0;
+    if (tid == 0) {
+        for (int s = 0; s < a.nstage; ++s) mbar_init(&bars[s], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        pol = l2_evict_first_policy();
+        for (int s = 0; s < a.nstage; ++s) {
+            const int64_t tl = blockIdx.x + s * grid;
+            if (tl < ntiles) {
+                const int64_t i0 = tl * P;
+                const int cnt = (int)min((int64_t)P, a.batch - i0);
+                const unsigned bytes = ((unsigned)cnt * NX * (unsigned)sizeof(S)) & ~15u;
+                mbar_arrive_expect_tx(&bars[s], bytes);
+                if (bytes) bulk_g2s(xbase + s * xstage, static_cast<const S*>(a.X) + i0 * NX, bytes, &bars[s], pol);
+            }
+        }
+    }
+    int it = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += grid, ++it) {
+        const int s = it % a.nstage;
+        S* xt = reinterpret_cast<S*>(xbase + s * xstage);
+        const int64_t inst0 = tile * P;
+        const int cnt = (int)min((int64_t)P, a.batch - inst0);
+        bool ok = mbar_wait_bounded(&bars[s], (unsigned)(it / a.nstage) & 1u, a.err);
+        const unsigned bytes = (unsigned)cnt * NX * (unsigned)sizeof(S);
+        const unsigned b16 = bytes & ~15u;
+        if (bytes != b16) {
+            const S* src = static_cast<const S*>(a.X) + inst0 * NX;
+            for (int e = b16 / sizeof(S) + tid; e < cnt * NX; e += kTcThreads) xt[e] = src[e];
+            __syncthreads();
+        }
+        if (ok) {
+            for (int q0 = warp * G; q0 < cnt; q0 += G * (kTcThreads / 32)) {
+                const S* xg = xt + q0 * NX;
+                S* yg = static_cast<S*>(a.Y) + (inst0 + q0) * NX;
+                const int live = cnt - q0;   // instances q < live of this group exist
+                if constexpr (FAST)
+                    tc2s_group_fast<S, N>(f, L, xg, yg, live, ex, ex_s);
+                else
+                    tc2s_group_any<S, N>(a, f, xg, yg, live, ex, ex_s);
+            }
+        }
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                for (int j = it; j < it + a.nstage; ++j)
+                    if (blockIdx.x + (int64_t)j * grid < ntiles)
+                        mbar_wait_bounded(&bars[j % a.nstage], (unsigned)(j / a.nstage) & 1u, a.err);
+            }
+            return;
+        }
+        if (tid == 0) {
+            const int64_t next = tile + a.nstage * grid;
+            if (next < ntiles) {
+                const int64_t i0 = next * P;
+                const int c2 = (int)min((int64_t)P, a.batch - i0);
+                const unsigned nb = ((unsigned)c2 * NX * (unsigned)sizeof(S)) & ~15u;
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&bars[s], nb);
+                if (nb) bulk_g2s(xt, static_cast<const S*>(a.X) + i0 * NX, nb, &bars[s], pol);
+            }
+        }
     }
 }
 
@@ -852,24 +1466,50 @@ static kron_status launch_tc2_n(const KronDesc& d, cudaStream_t st) {
     a.beta = (float)d.beta;
     a.beta_zero = d.beta == 0.0;
     a.alpha_one = d.alpha == 1.0;
+    a.ypair = ((uintptr_t)d.Y % (2 * sizeof(S))) == 0;
     a.err = device_error_word();
     if (!a.err) return KRON_ERR_CUDA;
+    // Body: the stacked one (KRON_VARIANT_EXCHANGE: intermediates through the
+    // warp's exchange rows; 9 <= n <= 16) or the padded tile per instance
+    // (KRON_VARIANT_IN_PLACE: the second product takes the first's accumulators).
+    // Measured defaults (HBM fraction, stacked against padded): FP32 n = 10, 12, 14:
+    // 0.80, 0.91, 0.87 against 0.48, 0.71, 0.81 -- stacked; 16-bit n = 10, 12: 0.55,
+    // 0.67 against 0.30, 0.44 -- stacked; 16-bit n = 14 and every storage at n = 16
+    // (where the padded tile wastes nothing): padded; odd n (eight instances per
+    // group, the slow general path): padded.
+    constexpr bool kStackable = N >= 9 && N <= 16;
+    if (d.variant == KRON_VARIANT_EXCHANGE && !kStackable) return KRON_ERR_NOT_SUPPORTED;
+    constexpr bool kStackedDefault = kStackable && (N == 10 || N == 12 || (N == 14 && sizeof(S) == 4));
+    const bool stacked = kStackable && (d.variant == KRON_VARIANT_EXCHANGE ||
+                                        (d.variant == KRON_VARIANT_AUTO && kStackedDefault));
     // Measured defaults: at n = 16, 32 KB operand tiles (32 FP32 or 64 bf16
     // instances; three / two stages); below 16 instances of fewer bytes, 16 per tile
     // and three stages (more resident CTAs).
     int P = d.P > 0 ? d.P : (N == 16 ? (sizeof(S) == 4 ? 32 : 64) : 16);
+    if (stacked && d.P <= 0) P = sizeof(S) == 4 ? 32 : 64;
     int mult = 1;
     while ((mult * N * N * sizeof(S)) % 16) ++mult;
     P = (P + mult - 1) / mult * mult;
     int nstage = d.nstage >= 1 ? d.nstage : ((N == 16 && sizeof(S) == 2) ? 2 : 3);
+    if (stacked && d.nstage < 1) nstage = sizeof(S) == 4 ? 3 : 2;
     if (nstage > 8) nstage = 8;
-    auto smem_of = [&](int ns) { return 128 + ns * round_up((size_t)P * N * N * sizeof(S), 128); };
+    const size_t exch = stacked ? (size_t)(kTcThreads / 32) * tc2s_group(N) * N * kTc2sRow : 0;
+    auto smem_of = [&](int ns) { return 128 + ns * round_up((size_t)P * N * N * sizeof(S), 128) + exch; };
     size_t smem = smem_of(nstage);
     while (nstage > 1 && smem > dev.smem_per_block_optin) smem = smem_of(--nstage);
     if (smem > dev.smem_per_block_optin) return KRON_ERR_NOT_SUPPORTED;
     a.P = P;
     a.nstage = nstage;
-    auto kern = tc2_kernel<S, N>;
+    void (*kern)(const TcArgs2<N>) = tc2_kernel<S, N>;
+    if constexpr (kStackable) {
+        if (stacked) {
+            kern = tc2s_kernel<S, N, false>;
+            if constexpr (N % 2 == 0) {
+                const bool fast = a.alpha_one && a.beta_zero && a.ypair && (!std::is_same<S, __half>::value || a.f16a);
+                if (fast) kern = tc2s_kernel<S, N, true>;
+            }
+        }
+    }
     if (!ensure_smem_optin((const void*)kern, smem)) return KRON_ERR_CUDA;
     const int64_t ntiles = (d.batch + P - 1) / P;
     int64_t grid = d.grid;
@@ -916,9 +1556,10 @@ static kron_status launch_tc3_n(const KronDesc& d, cudaStream_t st) {
     // compute_warps 1: the single-warp kernel; else W warps share an instance.
     // Measured default: four warps at n = 14, 15, 16 (seven or eight plane pairs
     // to share), one below (too few pairs to balance the barrier) and for f16
-    // storage at odd n (measured 3x slower with several warps; not understood).
-    const bool odd16 = std::is_same<S, __half>::value && (N & 1);
-    const int W = d.warps > 0 ? d.warps : ((N >= 14 && !odd16) ? 4 : 1);
+    // storage below n = 16 (measured 2-6x slower with several warps at n = 10,
+    // 12 and odd n; not understood).
+    const bool f16few = std::is_same<S, __half>::value && N != 16;
+    const int W = d.warps > 0 ? d.warps : ((N >= 14 && !f16few) ? 4 : 1);
     if (W != 1) {
         const size_t smem = 128 + 2 * (size_t)L::XB + L::TB;
         if (W > 8 || smem > dev.smem_per_block_optin) return KRON_ERR_NOT_SUPPORTED;

@@ -83,6 +83,13 @@ bool real_io(kron_dtype io) { return io == KRON_R32F || io == KRON_R64F || io ==
 // Whether kernel body `variant` exists for (kind, n, io, comp) and takes tile size P.
 bool variant_ok(int kind, int n, kron_dtype io, kron_compute comp, int variant, int P) {
     if (variant == KRON_VARIANT_AUTO) return true;
+    if (kind == 2 && comp == KRON_COMPUTE_32F_BF16X3 && real_io(io) && io != KRON_R64F) {
+        // 2-D split tensor bodies: one padded 16 x 16 tile per instance (in place:
+        // the second product takes the first's accumulators), or instances
+        // stacked along the MMA's N dimension through exchange rows (9 <= n <= 16)
+        if (variant == KRON_VARIANT_IN_PLACE) return true;
+        return variant == KRON_VARIANT_EXCHANGE && n >= 9;
+    }
     if (comp != KRON_COMPUTE_NATIVE || !real_io(io)) return false;
     const bool f32 = io == KRON_R32F, half = io == KRON_R16BF || io == KRON_R16F;
     switch (variant) {
@@ -270,8 +277,20 @@ KRON_API kron_status kron_autotune_config(kron_stream_t stream, int kind, int n,
         if (kind == 3 && comp == KRON_COMPUTE_32F_BF16X3) {
             for (int w : {1, 2, 4, 8}) cands.push_back(kron_kernel_config{0, 0, 0, 0, w});
         } else {
-            for (int mul2 : {1, 2, 4, 8})
-                for (int ns : {1, 2}) cands.push_back(kron_kernel_config{0, std::max(1, base * mul2 / 2), ns, 0, 0});
+            if (kind == 2 && comp == KRON_COMPUTE_32F_BF16X3 && real_io(io)) {
+                // the 2-D split tensor bodies (padded tile; stacked for 9 <= n <= 16):
+                // tiles of half to four times "one instance per thread" and of 32-128
+                // instances, one to three tiles in flight
+                for (int var : {(int)KRON_VARIANT_IN_PLACE, (int)KRON_VARIANT_EXCHANGE}) {
+                    if (!variant_ok(kind, n, io, comp, var, 0)) continue;
+                    for (int P : {0, base / 2, base, 2 * base, 4 * base, 32, 64, 128})
+                        for (int ns : {1, 2, 3})
+                            if (P > 0 || ns == 1) cands.push_back(kron_kernel_config{var, P > 0 ? P : 0, P > 0 ? ns : 0, 0, 0});
+                }
+            } else {
+                for (int mul2 : {1, 2, 4, 8})
+                    for (int ns : {1, 2}) cands.push_back(kron_kernel_config{0, std::max(1, base * mul2 / 2), ns, 0, 0});
+            }
         }
     }
     cudaEvent_t e0, e1;

@@ -213,7 +213,17 @@ def test_kernel_config_validation_and_round_trip(lib):
     assert lib.kron_set_kernel_config(2, 12, f32, 0, ctypes.byref(cfg(1, 0, 0, 0))) == NOTSUP_   # no in-place 2-D n=12
     assert lib.kron_set_kernel_config(2, 7, f32, 0, ctypes.byref(cfg(2, 0, 0, 0))) == NOTSUP_    # pairs need even n
     assert lib.kron_set_kernel_config(2, 16, kg.DTYPES["f64"], 0, ctypes.byref(cfg(2, 0, 0, 0))) == NOTSUP_
-    assert lib.kron_set_kernel_config(2, 16, f32, 1, ctypes.byref(cfg(3, 0, 0, 0))) == NOTSUP_   # tensor path: one body
+    # split tensor path: 2-D padded tile (any n) or stacked (9 <= n <= 16); 3-D one body
+    assert lib.kron_set_kernel_config(2, 16, f32, 1, ctypes.byref(cfg(3, 0, 0, 0))) == NOTSUP_
+    assert lib.kron_set_kernel_config(2, 8, f32, 1, ctypes.byref(cfg(2, 0, 0, 0))) == NOTSUP_
+    assert lib.kron_set_kernel_config(3, 16, f32, 1, ctypes.byref(cfg(2, 0, 0, 0))) == NOTSUP_
+    assert lib.kron_set_kernel_config(2, 16, kg.DTYPES["f64"], 1, ctypes.byref(cfg(1, 0, 0, 0))) == NOTSUP_
+    for n, var in ((8, 1), (9, 2), (12, 1), (16, 2)):
+        assert lib.kron_set_kernel_config(2, n, kg.DTYPES["bf16"], 1, ctypes.byref(cfg(var, 64, 2, 0))) == 0
+        got = cfg()
+        assert lib.kron_get_kernel_config(2, n, kg.DTYPES["bf16"], 1, ctypes.byref(got)) == 0
+        assert (got.variant, got.instances_per_tile, got.pipeline_depth) == (var, 64, 2)
+        assert lib.kron_set_kernel_config(2, n, kg.DTYPES["bf16"], 1, ctypes.byref(cfg())) == 0
     assert lib.kron_set_kernel_config(2, 16, f32, 0, ctypes.byref(cfg(1, 7, 0, 0))) == NOTSUP_   # in place: 8..32 by 8
     assert lib.kron_set_kernel_config(2, 16, kg.DTYPES["bf16"], 0, ctypes.byref(cfg(1, 32, 0, 0))) == NOTSUP_
     # compute warps: only the FP32 2-D n = 16 in-place body, in groups of P / 4

@@ -258,3 +258,73 @@ def test_bf16x3_3d_warps_per_instance(io, n):
         assert max_norm_err(outs[0], oracle_ref(b, X64), b, X64) <= 1e-5
     else:
         assert storage_check(outs[0], b, X64, io, compute="bf16x3") <= 1.0
+
+
+# --- 2-D stacked body: G = 8 / gcd(n, 8) instances side by side along the MMA's N
+# dimension, intermediates through per-warp exchange rows (variant "exchange") ---------
+def _stacked_and_padded(b, io, guard, alpha=1.0, beta=0.0, Y0=None, P=0, depth=0):
+    n, outs = b.n, {}
+    try:
+        for var in ("in_place", "exchange"):
+            kg.set_kernel_config(2, n, io, "bf16x3", variant=var, instances_per_tile=P, pipeline_depth=depth)
+            assert kg.get_kernel_config(2, n, io, "bf16x3")["variant"] == var
+            outs[var], X64 = run_gpu(b, io=io, compute="bf16x3", alpha=alpha, beta=beta, Y0=Y0, guard=guard)
+    finally:
+        kg.set_kernel_config(2, n, io, "bf16x3")
+    return outs, X64
+
+
+def _check_tc(Y, b, X64, io, **kw):
+    if io == "f32":
+        ref = oracle_ref(b, X64, **({} if kw.get("beta", 0.0) == 0.0 else
+                                    dict(alpha=kw["alpha"], beta=kw["beta"], Y=np.array(kw["Y0"], np.float64))))
+        tol = 1e-5 if kw.get("beta", 0.0) == 0.0 else 2 * bound(2, b.n) + 1e-6
+        assert max_norm_err(Y, ref, b, X64) <= tol
+    else:
+        assert storage_check(Y, b, X64, io, compute="bf16x3", **kw) <= 1.0
+
+
+@pytest.mark.parametrize("io", ["f32", "bf16", "f16"])
+@pytest.mark.parametrize("n", [9, 10, 11, 12, 13, 14, 15, 16])
+@pytest.mark.parametrize("guard", [8, 7])
+def test_bf16x3_2d_stacked_body(io, n, guard):
+    """Ragged batch (the last tile and the last group half filled); Y at an offset
+    where results leave as pairs (guard 8) and where they cannot (guard 7).  The two
+    bodies form every output from the same MMA products in the same order, so they
+    agree bit for bit."""
+    b = inputs.make_batch(2, n, 1037, seed=410 + n, x_dist="normal")
+    outs, X64 = _stacked_and_padded(b, io, guard)
+    _check_tc(outs["exchange"], b, X64, io)
+    assert np.array_equal(outs["exchange"], outs["in_place"])
+
+
+@pytest.mark.parametrize("io", ["f32", "bf16"])
+@pytest.mark.parametrize("n", [12, 13])
+@pytest.mark.parametrize("P,depth", [(5, 1), (24, 2), (40, 3), (128, 1)])
+def test_bf16x3_2d_stacked_any_tile(io, n, P, depth):
+    """Tiles that are not a whole number of groups, and every ring depth."""
+    b = inputs.make_batch(2, n, 2003, seed=430 + n + P, x_dist="normal")
+    outs, X64 = _stacked_and_padded(b, io, 8, P=P, depth=depth)
+    _check_tc(outs["exchange"], b, X64, io)
+
+
+@pytest.mark.parametrize("io", ["f32", "bf16", "f16"])
+@pytest.mark.parametrize("n", [12, 15])
+def test_bf16x3_2d_stacked_alpha_beta(io, n):
+    b = inputs.make_batch(2, n, 301, seed=440 + n, x_dist="normal")
+    rng = np.random.default_rng(3)
+    Y0 = rng.standard_normal(b.batch * n * n).astype(np.float32)
+    if io != "f32":
+        Y0 = storage_x(inputs.Batch(2, n, b.batch, b.A, b.B, None, Y0), io)[1]
+    Y0 = np.asarray(Y0, np.float64)
+    outs, X64 = _stacked_and_padded(b, io, 8, alpha=0.75, beta=-2.0, Y0=Y0)
+    _check_tc(outs["exchange"], b, X64, io, alpha=0.75, beta=-2.0, Y0=Y0)
+
+
+@pytest.mark.parametrize("io", ["bf16", "f16"])
+def test_bf16x3_2d_stacked_identity_is_exact(io):
+    b = inputs.make_batch(2, 12, 203, seed=450)
+    I = np.eye(12).ravel(order="F").astype(np.float32)
+    b.A, b.B = I, I.copy()
+    outs, X64 = _stacked_and_padded(b, io, 8)
+    assert np.array_equal(outs["exchange"], X64)
