@@ -406,7 +406,8 @@ def measure_variant(kg, name, steps, warmup, torch, dev, peaks, tune=True):
     gbs = by / (kern_ms * 1e-3) / 1e9
     r = {"gflops": round(fl / (kern_ms * 1e-3) / 1e9, 1), "hbm_gbs": round(gbs, 1),
          "hbm_frac": round(gbs / peaks["hbm"], 4), "ms": round(kern_ms, 4), "batch": b.batch,
-         "kernel": kernel_of(b.kind, b.n, wl["io"], wl["compute"], (tile or {}).get("variant", "auto")),
+         "kernel": kernel_of(b.kind, b.n, wl["io"], wl["compute"], (tile or {}).get("variant", "auto"),
+                             (tile or {}).get("compute_warps", 0)),
          "max_norm_err_vs_fp64_oracle": err,
          "tuned_config": tile}
     if wl["io"] in ("bf16", "f16"):
@@ -539,11 +540,11 @@ def measure_interfaces(kg, steps, warmup, torch, dev, peaks):
     return out
 
 
-def kernel_of(kind, n, io, compute, variant="auto"):
+def kernel_of(kind, n, io, compute, variant="auto", warps=0):
     """Name of the kernel the library dispatches a contiguous batch to (with the
-    kernel body the tuning table holds for it)."""
+    kernel body and compute warps the tuning table holds for it)."""
     if compute == "bf16x3":
-        if kind == 3 and n >= 14 and not (io == "f16" and n != 16):
+        if kind == 3 and (warps > 1 or (warps == 0 and n >= 14 and not (io == "f16" and n != 16))):
             return f"tc3g_kernel<n={n},{io}>"   # several warps share an instance
         if kind == 2 and (variant == "exchange" or (
                 variant == "auto" and (n in (10, 12) or (n == 14 and io == "f32")))):
