@@ -547,7 +547,7 @@ def kernel_of(kind, n, io, compute, variant="auto", warps=0):
         if kind == 3 and (warps > 1 or (warps == 0 and n >= 14 and not (io == "f16" and n != 16))):
             return f"tc3g_kernel<n={n},{io}>"   # several warps share an instance
         if kind == 2 and (variant == "exchange" or (
-                variant == "auto" and (n in (10, 12) or (n == 14 and io == "f32")))):
+                variant == "auto" and n >= 10 and n % 2 == 0 and not (n == 16 and io == "f32"))):
             return f"tc2s_kernel<n={n},{io}>"   # instances stacked along the MMA's N dimension
         return f"tc{kind}_kernel<n={n},{io}>"
     if io in ("c64", "c128") or variant == "scalar":

@@ -294,7 +294,9 @@ KRON_API kron_status kron_autotune(kron_stream_t stream, int kind, int n, int64_
  *   pipeline_depth:     tiles in flight per CTA (0 = default, 1..8)
  *   fibers_per_step:    register blocking of the last contraction of the
  *                       packed-pair bodies: 1 or 2 fibers per thread and step
- *                       (0 = default)
+ *                       (0 = default); for the stacked 2-D split tensor body
+ *                       (even n, plain epilogue), 1 or 2 groups of stacked
+ *                       instances per warp step
  *   compute_warps:      compute warps per CTA (0 = default).  The FP32 2-D
  *                       in-place bodies take it -- n = 16: groups of
  *                       instances_per_tile / 4 warps; n = 10, 14: groups of
@@ -328,8 +330,9 @@ KRON_API kron_status kron_autotune(kron_stream_t stream, int kind, int n, int64_
  * instances side by side along the MMA's N dimension with the intermediate
  * passed through per-warp exchange rows in shared memory, so that only the
  * contracted dimension and the component rows are padded.  The built-in
- * choice is the stacked body for n = 10 and 12 (and FP32 at n = 14) and the
- * padded one otherwise; both give the same bits.  The 3-D split tensor path and complex storage have one body
+ * choice is the stacked body for even n >= 10 except FP32 at n = 16 (with two
+ * groups per warp step for 16-bit storage at n = 14, 16) and the padded one
+ * otherwise; both give the same bits.  The 3-D split tensor path and complex storage have one body
  * each: only instances_per_tile and pipeline_depth apply there (and
  * compute_warps for the 3-D tensor body).
  *

@@ -1168,115 +1168,121 @@ __device__ __forceinline__ void tc2s_lane_init(Tc2sLane<N>& L, int g, int t) {
     }
 }
 
-// A group of an even n with the plain epilogue (alpha = 1, beta = 0, Y aligned to
-// pairs): offsets from the lane's table, and the MMAs issued step by step across
-// the n-tiles (every n-tile's first product, then every second, ...), so that the
-// dependent products of one n-tile are separated by the independent ones of the
-// others.  In the last, partial group the operand slots of absent instances
-// (q >= live) are read as they are -- stale values of the ring or the exchange
-// rows after it, inside the CTA's shared memory (at most G - 1 instances past a
-// tile) -- and only their stores are skipped: every column of W and every
-// stacked row of the result depends on its own instance alone.
-template <typename S, int N>
+// K consecutive groups of an even n with the plain epilogue (alpha = 1, beta = 0,
+// Y aligned to pairs): offsets from the lane's table (group k adds k G instances
+// and k G n exchange rows), and the MMAs issued step by step across the K NT
+// (group, n-tile) chains (every chain's first product, then every second, ...), so
+// that the dependent products of one chain are separated by the independent ones
+// of the others.  In the last, partial groups the operand slots of absent
+// instances (q >= live) are read as they are -- stale values of the ring or the
+// exchange rows after it, inside the CTA's shared memory (at most K G - 1
+// instances past a tile) -- and only their stores are skipped: every column of W
+// and every stacked row of the result depends on its own instance alone.
+template <typename S, int N, int K>
 __device__ __forceinline__ void tc2s_group_fast(const Tc2sFrags& f, const Tc2sLane<N>& L, const S* xg, S* yg,
                                                 int live, unsigned char* ex, uint32_t ex_s) {
-    constexpr int NT = Tc2sLane<N>::NT;
+    constexpr int NT = Tc2sLane<N>::NT, CH = K * NT, G = tc2s_group(N);
+    constexpr int XG = G * N * N, EG = G * N * kTc2sRow;   // per group: operand elements, exchange bytes
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     const bool k8 = 2 * t + 8 < N;   // the lane's rows 2t + 8, 2t + 9 exist
     const bool r8 = g + 8 < N;       // the lane's W row / Y column g + 8 exists
     // ---- stage 1 ----------------------------------------------------------------------------
-    float w[NT][4];
+    float w[CH][4];
 #pragma unroll
-    for (int nt = 0; nt < NT; ++nt)
+    for (int c = 0; c < CH; ++c)
 #pragma unroll
-        for (int e = 0; e < 4; ++e) w[nt][e] = 0.f;
+        for (int e = 0; e < 4; ++e) w[c][e] = 0.f;
     if constexpr (sizeof(S) == 2) {
-        unsigned b0[NT], b1[NT];
+        unsigned b0[CH], b1[CH];
 #pragma unroll
-        for (int nt = 0; nt < NT; ++nt) {
-            const unsigned* xp = reinterpret_cast<const unsigned*>(xg + L.xo[nt]);
-            b0[nt] = xp[0];
-            b1[nt] = k8 ? xp[4] : 0u;
+        for (int c = 0; c < CH; ++c) {
+            const unsigned* xp = reinterpret_cast<const unsigned*>(xg + (c / NT) * XG + L.xo[c % NT]);
+            b0[c] = xp[0];
+            b1[c] = k8 ? xp[4] : 0u;
         }
         if constexpr (std::is_same<S, __half>::value) {
 #pragma unroll
-            for (int nt = 0; nt < NT; ++nt) mma_f16_16816(w[nt], f.f1l, b0[nt], b1[nt]);
+            for (int c = 0; c < CH; ++c) mma_f16_16816(w[c], f.f1l, b0[c], b1[c]);
 #pragma unroll
-            for (int nt = 0; nt < NT; ++nt) mma_f16_16816(w[nt], f.f1h, b0[nt], b1[nt]);
+            for (int c = 0; c < CH; ++c) mma_f16_16816(w[c], f.f1h, b0[c], b1[c]);
         } else {
 #pragma unroll
-            for (int nt = 0; nt < NT; ++nt) mma_bf16_16816(w[nt], f.m1l, b0[nt], b1[nt]);
+            for (int c = 0; c < CH; ++c) mma_bf16_16816(w[c], f.m1l, b0[c], b1[c]);
 #pragma unroll
-            for (int nt = 0; nt < NT; ++nt) mma_bf16_16816(w[nt], f.m1h, b0[nt], b1[nt]);
+            for (int c = 0; c < CH; ++c) mma_bf16_16816(w[c], f.m1h, b0[c], b1[c]);
         }
     } else {
-        unsigned bh0[NT], bl0[NT], bh1[NT], bl1[NT];
+        unsigned bh0[CH], bl0[CH], bh1[CH], bl1[CH];
 #pragma unroll
-        for (int nt = 0; nt < NT; ++nt) {
-            const float2 p0 = *reinterpret_cast<const float2*>(xg + L.xo[nt]);
-            const float2 p1 = k8 ? *reinterpret_cast<const float2*>(xg + L.xo[nt] + 8) : make_float2(0.f, 0.f);
-            split_pair(p0.x, p0.y, bh0[nt], bl0[nt]);
-            split_pair(p1.x, p1.y, bh1[nt], bl1[nt]);
+        for (int c = 0; c < CH; ++c) {
+            const S* xp = xg + (c / NT) * XG + L.xo[c % NT];
+            const float2 p0 = *reinterpret_cast<const float2*>(xp);
+            const float2 p1 = k8 ? *reinterpret_cast<const float2*>(xp + 8) : make_float2(0.f, 0.f);
+            split_pair(p0.x, p0.y, bh0[c], bl0[c]);
+            split_pair(p1.x, p1.y, bh1[c], bl1[c]);
         }
 #pragma unroll
-        for (int nt = 0; nt < NT; ++nt) mma_bf16_16816(w[nt], f.m1l, bh0[nt], bh1[nt]);
+        for (int c = 0; c < CH; ++c) mma_bf16_16816(w[c], f.m1l, bh0[c], bh1[c]);
 #pragma unroll
-        for (int nt = 0; nt < NT; ++nt) mma_bf16_16816(w[nt], f.m1h, bl0[nt], bl1[nt]);
+        for (int c = 0; c < CH; ++c) mma_bf16_16816(w[c], f.m1h, bl0[c], bl1[c]);
 #pragma unroll
-        for (int nt = 0; nt < NT; ++nt) mma_bf16_16816(w[nt], f.m1h, bh0[nt], bh1[nt]);
+        for (int c = 0; c < CH; ++c) mma_bf16_16816(w[c], f.m1h, bh0[c], bh1[c]);
     }
 #pragma unroll
-    for (int nt = 0; nt < NT; ++nt) {
+    for (int c = 0; c < CH; ++c) {
+        unsigned char* e0 = ex + (c / NT) * EG + L.eo[c % NT];
         unsigned hi, lo;
-        split_pair(w[nt][0], w[nt][1], hi, lo);
-        *reinterpret_cast<unsigned*>(ex + L.eo[nt]) = hi;
-        *reinterpret_cast<unsigned*>(ex + L.eo[nt] + 32) = lo;
+        split_pair(w[c][0], w[c][1], hi, lo);
+        *reinterpret_cast<unsigned*>(e0) = hi;
+        *reinterpret_cast<unsigned*>(e0 + 32) = lo;
         if (r8) {
-            split_pair(w[nt][2], w[nt][3], hi, lo);
-            *reinterpret_cast<unsigned*>(ex + L.eo[nt] + 8 * kTc2sRow) = hi;
-            *reinterpret_cast<unsigned*>(ex + L.eo[nt] + 8 * kTc2sRow + 32) = lo;
+            split_pair(w[c][2], w[c][3], hi, lo);
+            *reinterpret_cast<unsigned*>(e0 + 8 * kTc2sRow) = hi;
+            *reinterpret_cast<unsigned*>(e0 + 8 * kTc2sRow + 32) = lo;
         }
     }
     __syncwarp();
     // ---- stage 2 ----------------------------------------------------------------------------
     const uint32_t lrow = ex_s + (lane & 7) * kTc2sRow + (lane >> 3) * 16;
-    unsigned b[NT][4];
-    float y[NT][4];
+    unsigned b[CH][4];
+    float y[CH][4];
 #pragma unroll
-    for (int nt = 0; nt < NT; ++nt) {
-        ldsm_x4(b[nt], lrow + nt * 8 * kTc2sRow);
+    for (int c = 0; c < CH; ++c) {
+        ldsm_x4(b[c], lrow + (c / NT) * EG + (c % NT) * 8 * kTc2sRow);
 #pragma unroll
-        for (int e = 0; e < 4; ++e) y[nt][e] = 0.f;
+        for (int e = 0; e < 4; ++e) y[c][e] = 0.f;
     }
-    __syncwarp();   // exchange rows read: the next group may overwrite them
+    __syncwarp();   // exchange rows read: the next groups may overwrite them
 #pragma unroll
-    for (int nt = 0; nt < NT; ++nt) mma_bf16_16816(y[nt], f.m2h, b[nt][2], b[nt][3]);
+    for (int c = 0; c < CH; ++c) mma_bf16_16816(y[c], f.m2h, b[c][2], b[c][3]);
 #pragma unroll
-    for (int nt = 0; nt < NT; ++nt) mma_bf16_16816(y[nt], f.m2l, b[nt][0], b[nt][1]);
+    for (int c = 0; c < CH; ++c) mma_bf16_16816(y[c], f.m2l, b[c][0], b[c][1]);
 #pragma unroll
-    for (int nt = 0; nt < NT; ++nt) mma_bf16_16816(y[nt], f.m2h, b[nt][0], b[nt][1]);
+    for (int c = 0; c < CH; ++c) mma_bf16_16816(y[c], f.m2h, b[c][0], b[c][1]);
 #pragma unroll
-    for (int nt = 0; nt < NT; ++nt) {
-        if (L.qy[nt] >= live) continue;
-        S* dst = yg + L.yo[nt];
+    for (int c = 0; c < CH; ++c) {
+        if ((c / NT) * G + L.qy[c % NT] >= live) continue;
+        S* dst = yg + (c / NT) * XG + L.yo[c % NT];
         if constexpr (sizeof(S) == 4) {
-            __stcs(reinterpret_cast<float2*>(dst), make_float2(y[nt][0], y[nt][1]));
-            if (r8) __stcs(reinterpret_cast<float2*>(dst + 8 * N), make_float2(y[nt][2], y[nt][3]));
+            __stcs(reinterpret_cast<float2*>(dst), make_float2(y[c][0], y[c][1]));
+            if (r8) __stcs(reinterpret_cast<float2*>(dst + 8 * N), make_float2(y[c][2], y[c][3]));
         } else {
-            __stcs(reinterpret_cast<unsigned*>(dst), pack16<S>(f2_pack(y[nt][0], y[nt][1])));
-            if (r8) __stcs(reinterpret_cast<unsigned*>(dst + 8 * N), pack16<S>(f2_pack(y[nt][2], y[nt][3])));
+            __stcs(reinterpret_cast<unsigned*>(dst), pack16<S>(f2_pack(y[c][0], y[c][1])));
+            if (r8) __stcs(reinterpret_cast<unsigned*>(dst + 8 * N), pack16<S>(f2_pack(y[c][2], y[c][3])));
         }
     }
 }
 
-// FAST: every group by tc2s_group_fast (even n, plain epilogue, the stored operand
-// entering the MMAs as it is or split from FP32); else by tc2s_group_any.  The two
-// bodies are separate kernels: one kernel never chooses between them at run time.
-template <typename S, int N, bool FAST>
+// FAST: every K groups by tc2s_group_fast (even n, plain epilogue, the stored
+// operand entering the MMAs as it is or split from FP32); else every group by
+// tc2s_group_any.  The two bodies are separate kernels: one kernel never chooses
+// between them at run time.
+template <typename S, int N, bool FAST, int K>
 __global__ void __launch_bounds__(kTcThreads) tc2s_kernel(const __grid_constant__ TcArgs2<N> a) {
     constexpr int NX = N * N, G = tc2s_group(N);
     static_assert(N >= 9 && N <= 16 && (G * N) % 8 == 0, "stacked body: 9 <= n <= 16");
     static_assert(!FAST || N % 2 == 0, "the fast body takes even n");
+    static_assert(K == 1 || (FAST && K == 2), "two groups per step in the fast body only");
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
     const int P = a.P;
@@ -1286,9 +1292,9 @@ __global__ void __launch_bounds__(kTcThreads) tc2s_kernel(const __grid_constant_
     const int g = lane >> 2, t = lane & 3;
     const int64_t ntiles = (a.batch + P - 1) / P;
     const int64_t grid = gridDim.x;
-    unsigned char* ex = xbase + a.nstage * xstage + warp * (G * N * kTc2sRow);
+    unsigned char* ex = xbase + a.nstage * xstage + warp * (K * G * N * kTc2sRow);
     const uint32_t ex_s = (uint32_t)__cvta_generic_to_shared(ex);
-    for (int e = lane; e < G * N * kTc2sRow / 4; e += 32) reinterpret_cast<unsigned*>(ex)[e] = 0u;
+    for (int e = lane; e < K * G * N * kTc2sRow / 4; e += 32) reinterpret_cast<unsigned*>(ex)[e] = 0u;
 
     Tc2sFrags f;
     for (int e = 0; e < 4; ++e) f.f1h[e] = f.f1l[e] = 0u;
@@ -1337,12 +1343,12 @@ __global__ void __launch_bounds__(kTcThreads) tc2s_kernel(const __grid_constant_
             __syncthreads();
         }
         if (ok) {
-            for (int q0 = warp * G; q0 < cnt; q0 += G * (kTcThreads / 32)) {
+            for (int q0 = warp * G * K; q0 < cnt; q0 += G * K * (kTcThreads / 32)) {
                 const S* xg = xt + q0 * NX;
                 S* yg = static_cast<S*>(a.Y) + (inst0 + q0) * NX;
                 const int live = cnt - q0;   // instances q < live of this group exist
                 if constexpr (FAST)
-                    tc2s_group_fast<S, N>(f, L, xg, yg, live, ex, ex_s);
+                    tc2s_group_fast<S, N, K>(f, L, xg, yg, live, ex, ex_s);
                 else
                     tc2s_group_any<S, N>(a, f, xg, yg, live, ex, ex_s);
             }
@@ -1474,26 +1480,31 @@ static kron_status launch_tc2_n(const KronDesc& d, cudaStream_t st) {
     // (KRON_VARIANT_IN_PLACE: the second product takes the first's accumulators).
     // Measured defaults (HBM fraction, stacked against padded): FP32 n = 10, 12, 14:
     // 0.80, 0.91, 0.87 against 0.48, 0.71, 0.81 -- stacked; 16-bit n = 10, 12: 0.55,
-    // 0.67 against 0.30, 0.44 -- stacked; 16-bit n = 14 and every storage at n = 16
-    // (where the padded tile wastes nothing): padded; odd n (eight instances per
-    // group, the slow general path): padded.
+    // 0.67 against 0.30, 0.44 -- stacked; 16-bit n = 14, 16 with two groups per warp
+    // step, 32-instance tiles, three in flight: 0.65, 0.93 against 0.60, 0.83-0.89 --
+    // stacked; FP32 n = 16 (the padded tile wastes nothing; 1.0): padded; odd n
+    // (eight instances per group, the slow general path): padded.
     constexpr bool kStackable = N >= 9 && N <= 16;
     if (d.variant == KRON_VARIANT_EXCHANGE && !kStackable) return KRON_ERR_NOT_SUPPORTED;
-    constexpr bool kStackedDefault = kStackable && (N == 10 || N == 12 || (N == 14 && sizeof(S) == 4));
+    constexpr bool kStackedDefault = kStackable && N % 2 == 0 && !(N == 16 && sizeof(S) == 4);
+    constexpr bool kTwoGroups = sizeof(S) == 2 && N >= 14;   // default groups per warp step: 2
     const bool stacked = kStackable && (d.variant == KRON_VARIANT_EXCHANGE ||
                                         (d.variant == KRON_VARIANT_AUTO && kStackedDefault));
     // Measured defaults: at n = 16, 32 KB operand tiles (32 FP32 or 64 bf16
     // instances; three / two stages); below 16 instances of fewer bytes, 16 per tile
     // and three stages (more resident CTAs).
     int P = d.P > 0 ? d.P : (N == 16 ? (sizeof(S) == 4 ? 32 : 64) : 16);
-    if (stacked && d.P <= 0) P = sizeof(S) == 4 ? 32 : 64;
+    if (stacked && d.P <= 0) P = (sizeof(S) == 4 || kTwoGroups) ? 32 : 64;
     int mult = 1;
     while ((mult * N * N * sizeof(S)) % 16) ++mult;
     P = (P + mult - 1) / mult * mult;
     int nstage = d.nstage >= 1 ? d.nstage : ((N == 16 && sizeof(S) == 2) ? 2 : 3);
-    if (stacked && d.nstage < 1) nstage = sizeof(S) == 4 ? 3 : 2;
+    if (stacked && d.nstage < 1) nstage = (sizeof(S) == 4 || kTwoGroups) ? 3 : 2;
     if (nstage > 8) nstage = 8;
-    const size_t exch = stacked ? (size_t)(kTcThreads / 32) * tc2s_group(N) * N * kTc2sRow : 0;
+    const bool fast = N % 2 == 0 && a.alpha_one && a.beta_zero && a.ypair &&
+                      (!std::is_same<S, __half>::value || a.f16a);
+    const int K = stacked && fast && (d.fps == 2 || (d.fps == 0 && kTwoGroups)) ? 2 : 1;   // groups per step
+    const size_t exch = stacked ? (size_t)(kTcThreads / 32) * K * tc2s_group(N) * N * kTc2sRow : 0;
     auto smem_of = [&](int ns) { return 128 + ns * round_up((size_t)P * N * N * sizeof(S), 128) + exch; };
     size_t smem = smem_of(nstage);
     while (nstage > 1 && smem > dev.smem_per_block_optin) smem = smem_of(--nstage);
@@ -1503,10 +1514,9 @@ static kron_status launch_tc2_n(const KronDesc& d, cudaStream_t st) {
     void (*kern)(const TcArgs2<N>) = tc2_kernel<S, N>;
     if constexpr (kStackable) {
         if (stacked) {
-            kern = tc2s_kernel<S, N, false>;
+            kern = tc2s_kernel<S, N, false, 1>;
             if constexpr (N % 2 == 0) {
-                const bool fast = a.alpha_one && a.beta_zero && a.ypair && (!std::is_same<S, __half>::value || a.f16a);
-                if (fast) kern = tc2s_kernel<S, N, true>;
+                if (fast) kern = K == 2 ? tc2s_kernel<S, N, true, 2> : tc2s_kernel<S, N, true, 1>;
             }
         }
     }

@@ -281,11 +281,16 @@ KRON_API kron_status kron_autotune_config(kron_stream_t stream, int kind, int n,
                 // the 2-D split tensor bodies (padded tile; stacked for 9 <= n <= 16):
                 // tiles of half to four times "one instance per thread" and of 32-128
                 // instances, one to three tiles in flight
+                // (the stacked body also with one or two groups per warp step: fibers_per_step)
                 for (int var : {(int)KRON_VARIANT_IN_PLACE, (int)KRON_VARIANT_EXCHANGE}) {
                     if (!variant_ok(kind, n, io, comp, var, 0)) continue;
-                    for (int P : {0, base / 2, base, 2 * base, 4 * base, 32, 64, 128})
-                        for (int ns : {1, 2, 3})
-                            if (P > 0 || ns == 1) cands.push_back(kron_kernel_config{var, P > 0 ? P : 0, P > 0 ? ns : 0, 0, 0});
+                    for (int fps : {0, 1, 2}) {
+                        if (fps && (var != KRON_VARIANT_EXCHANGE || n % 2)) continue;
+                        for (int P : {0, base / 2, base, 2 * base, 4 * base, 32, 64, 128})
+                            for (int ns : {1, 2, 3})
+                                if (P > 0 || ns == 1)
+                                    cands.push_back(kron_kernel_config{var, P > 0 ? P : 0, P > 0 ? ns : 0, fps, 0});
+                    }
                 }
             } else {
                 for (int mul2 : {1, 2, 4, 8})

@@ -27,7 +27,8 @@ def test_kernel_names_follow_dispatch():
     assert bench.kernel_of(2, 12, "bf16", "bf16x3").startswith("tc2s_kernel")
     assert bench.kernel_of(2, 12, "bf16", "bf16x3", "in_place").startswith("tc2_kernel")
     assert bench.kernel_of(2, 13, "f16", "bf16x3").startswith("tc2_kernel")
-    assert bench.kernel_of(2, 16, "bf16", "bf16x3").startswith("tc2_kernel")
+    assert bench.kernel_of(2, 16, "bf16", "bf16x3").startswith("tc2s_kernel")
+    assert bench.kernel_of(2, 16, "bf16", "bf16x3", "in_place").startswith("tc2_kernel")
     assert bench.kernel_of(2, 14, "f32", "bf16x3").startswith("tc2s_kernel")
     assert bench.kernel_of(2, 16, "bf16", "native").startswith("pair16h_kernel")
     assert bench.kernel_of(2, 10, "f32", "native").startswith("pair2ip_kernel")

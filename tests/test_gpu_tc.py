@@ -262,11 +262,12 @@ def test_bf16x3_3d_warps_per_instance(io, n):
 
 # --- 2-D stacked body: G = 8 / gcd(n, 8) instances side by side along the MMA's N
 # dimension, intermediates through per-warp exchange rows (variant "exchange") ---------
-def _stacked_and_padded(b, io, guard, alpha=1.0, beta=0.0, Y0=None, P=0, depth=0):
+def _stacked_and_padded(b, io, guard, alpha=1.0, beta=0.0, Y0=None, P=0, depth=0, groups=0):
     n, outs = b.n, {}
     try:
         for var in ("in_place", "exchange"):
-            kg.set_kernel_config(2, n, io, "bf16x3", variant=var, instances_per_tile=P, pipeline_depth=depth)
+            kg.set_kernel_config(2, n, io, "bf16x3", variant=var, instances_per_tile=P, pipeline_depth=depth,
+                                 fibers_per_step=groups if var == "exchange" else 0)
             assert kg.get_kernel_config(2, n, io, "bf16x3")["variant"] == var
             outs[var], X64 = run_gpu(b, io=io, compute="bf16x3", alpha=alpha, beta=beta, Y0=Y0, guard=guard)
     finally:
@@ -328,3 +329,15 @@ def test_bf16x3_2d_stacked_identity_is_exact(io):
     b.A, b.B = I, I.copy()
     outs, X64 = _stacked_and_padded(b, io, 8)
     assert np.array_equal(outs["exchange"], X64)
+
+
+@pytest.mark.parametrize("io", ["f32", "bf16", "f16"])
+@pytest.mark.parametrize("n", [10, 12, 14, 16])
+@pytest.mark.parametrize("P", [0, 40])
+def test_bf16x3_2d_stacked_two_groups_per_step(io, n, P):
+    """Two groups of stacked instances per warp step (fibers_per_step 2): the same bits as
+    the padded tile, with the last groups of a ragged batch partly or wholly absent."""
+    b = inputs.make_batch(2, n, 1037, seed=460 + n + P, x_dist="normal")
+    outs, X64 = _stacked_and_padded(b, io, 8, P=P, depth=2 if P else 0, groups=2)
+    _check_tc(outs["exchange"], b, X64, io)
+    assert np.array_equal(outs["exchange"], outs["in_place"])
