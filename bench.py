@@ -544,7 +544,8 @@ def kernel_of(kind, n, io, compute, variant="auto", warps=0):
     """Name of the kernel the library dispatches a contiguous batch to (with the
     kernel body and compute warps the tuning table holds for it)."""
     if compute == "bf16x3":
-        if kind == 3 and (warps > 1 or (warps == 0 and n >= 14 and not (io == "f16" and n != 16))):
+        if kind == 3 and (warps > 1 or (warps == 0 and (
+                (n >= 14 and not (io == "f16" and n != 16)) or (io == "f32" and n >= 10 and n % 2 == 0)))):
             return f"tc3g_kernel<n={n},{io}>"   # several warps share an instance
         if kind == 2 and (variant == "exchange" or (
                 variant == "auto" and n >= 10 and n % 2 == 0 and not (n == 16 and io == "f32"))):

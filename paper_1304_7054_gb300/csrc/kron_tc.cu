@@ -1565,11 +1565,13 @@ static kron_status launch_tc3_n(const KronDesc& d, cudaStream_t st) {
     using L = Tc3Layout<S, N>;
     // compute_warps 1: the single-warp kernel; else W warps share an instance.
     // Measured default: four warps at n = 14, 15, 16 (seven or eight plane pairs
-    // to share), one below (too few pairs to balance the barrier) and for f16
-    // storage below n = 16 (measured 2-6x slower with several warps at n = 10,
-    // 12 and odd n; not understood).
+    // to share) and for FP32 storage at n = 10, 12 (0.33 and 0.49 of HBM against
+    // 0.30 and 0.35 with one warp); one warp for 16-bit storage below n = 14 (bf16:
+    // the same speed; f16: several warps measured 2-6x slower at n = 10, 12 and odd
+    // n, not understood) and for smaller n (too few plane pairs to share).
     const bool f16few = std::is_same<S, __half>::value && N != 16;
-    const int W = d.warps > 0 ? d.warps : ((N >= 14 && !f16few) ? 4 : 1);
+    const bool f32mid = sizeof(S) == 4 && N >= 10 && N % 2 == 0;
+    const int W = d.warps > 0 ? d.warps : (((N >= 14 && !f16few) || f32mid) ? 4 : 1);
     if (W != 1) {
         const size_t smem = 128 + 2 * (size_t)L::XB + L::TB;
         if (W > 8 || smem > dev.smem_per_block_optin) return KRON_ERR_NOT_SUPPORTED;

@@ -41,7 +41,8 @@ def test_kernel_names_follow_dispatch():
     assert bench.kernel_of(3, 10, "f32", "native").startswith("pair3pk_kernel")
     assert bench.kernel_of(2, 16, "f64", "native").startswith("fiber_kernel")
     assert bench.kernel_of(3, 16, "f32", "bf16x3").startswith("tc3g_kernel")
-    assert bench.kernel_of(3, 10, "f32", "bf16x3").startswith("tc3_kernel")
+    assert bench.kernel_of(3, 10, "f32", "bf16x3").startswith("tc3g_kernel")
+    assert bench.kernel_of(3, 10, "bf16", "bf16x3").startswith("tc3_kernel")
     assert bench.kernel_of(3, 10, "f32", "bf16x3", "auto", 4).startswith("tc3g_kernel")
     assert bench.kernel_of(3, 16, "f32", "bf16x3", "auto", 1).startswith("tc3_kernel")
     assert bench.kernel_of(3, 15, "f16", "bf16x3").startswith("tc3_kernel")
