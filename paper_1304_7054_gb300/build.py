@@ -90,10 +90,10 @@ FAMILY_SOURCES = {
     "kron1_kernel": ["kron_kron1.cu", "kron_pair.cuh", "kron_fiber.cuh", "kron_device.cuh"],
     "kron1t_kernel": ["kron_kron1.cu", "kron_pair.cuh", "kron_fiber.cuh", "kron_device.cuh"],
     "gemm_a_tma_kernel": ["kron_gemm_a.cu", "kron_pair.cuh", "kron_fiber.cuh", "kron_device.cuh"],
-    "tc2_kernel": ["kron_tc.cu", "kron_fiber.cuh", "kron_device.cuh"],
-    "tc2s_kernel": ["kron_tc.cu", "kron_fiber.cuh", "kron_device.cuh"],
-    "tc3_kernel": ["kron_tc.cu", "kron_fiber.cuh", "kron_device.cuh"],
-    "tc3g_kernel": ["kron_tc.cu", "kron_fiber.cuh", "kron_device.cuh"],
+    "tc2_kernel": ["kron_tc2.cu", "kron_tc.cuh", "kron_fiber.cuh", "kron_device.cuh"],
+    "tc2s_kernel": ["kron_tc2.cu", "kron_tc.cuh", "kron_fiber.cuh", "kron_device.cuh"],
+    "tc3_kernel": ["kron_tc3.cu", "kron_tc.cuh", "kron_fiber.cuh", "kron_device.cuh"],
+    "tc3g_kernel": ["kron_tc3.cu", "kron_tc.cuh", "kron_fiber.cuh", "kron_device.cuh"],
     "varlen_kernel": ["kron_varlen.cu", "kron_fiber.cuh", "kron_device.cuh"],
 }
 
