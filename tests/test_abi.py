@@ -218,12 +218,13 @@ def test_kernel_config_validation_and_round_trip(lib):
     assert lib.kron_set_kernel_config(2, 8, f32, 1, ctypes.byref(cfg(2, 0, 0, 0))) == NOTSUP_
     assert lib.kron_set_kernel_config(3, 16, f32, 1, ctypes.byref(cfg(2, 0, 0, 0))) == NOTSUP_
     assert lib.kron_set_kernel_config(2, 16, kg.DTYPES["f64"], 1, ctypes.byref(cfg(1, 0, 0, 0))) == NOTSUP_
-    for n, var in ((8, 1), (9, 2), (12, 1), (16, 2)):
-        assert lib.kron_set_kernel_config(2, n, kg.DTYPES["bf16"], 1, ctypes.byref(cfg(var, 64, 2, 0))) == 0
+    for n, var, groups in ((8, 1, 0), (9, 2, 0), (12, 1, 0), (16, 2, 2), (14, 2, 1)):
+        assert lib.kron_set_kernel_config(2, n, kg.DTYPES["bf16"], 1, ctypes.byref(cfg(var, 64, 2, groups))) == 0
         got = cfg()
         assert lib.kron_get_kernel_config(2, n, kg.DTYPES["bf16"], 1, ctypes.byref(got)) == 0
-        assert (got.variant, got.instances_per_tile, got.pipeline_depth) == (var, 64, 2)
+        assert (got.variant, got.instances_per_tile, got.pipeline_depth, got.fibers_per_step) == (var, 64, 2, groups)
         assert lib.kron_set_kernel_config(2, n, kg.DTYPES["bf16"], 1, ctypes.byref(cfg())) == 0
+    assert lib.kron_set_kernel_config(2, 16, kg.DTYPES["bf16"], 1, ctypes.byref(cfg(2, 64, 2, 3))) == INVALID
     assert lib.kron_set_kernel_config(2, 16, f32, 0, ctypes.byref(cfg(1, 7, 0, 0))) == NOTSUP_   # in place: 8..32 by 8
     assert lib.kron_set_kernel_config(2, 16, kg.DTYPES["bf16"], 0, ctypes.byref(cfg(1, 32, 0, 0))) == NOTSUP_
     # compute warps: only the FP32 2-D n = 16 in-place body, in groups of P / 4
