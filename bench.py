@@ -56,6 +56,9 @@ WORKLOADS = {
     "kron3-f16-bf16x3-n16": dict(kind=3, n=16, batch=1 << 16, io="f16", compute="bf16x3", seed=4),
     "kron3-bf16x3-n15": dict(kind=3, n=15, batch=1 << 16, io="f32", compute="bf16x3", seed=4),
     "kron2-bf16-n8": dict(kind=2, n=8, batch=1 << 20, io="bf16", compute="native", seed=4),
+    "kron2-f16-n8": dict(kind=2, n=8, batch=1 << 20, io="f16", compute="native", seed=4),
+    "kron2-bf16-bf16x3-n8": dict(kind=2, n=8, batch=1 << 20, io="bf16", compute="bf16x3", seed=4),
+    "kron2-f16-bf16x3-n8": dict(kind=2, n=8, batch=1 << 20, io="f16", compute="bf16x3", seed=4),
     "kron2-bf16-n12": dict(kind=2, n=12, batch=1 << 20, io="bf16", compute="native", seed=4),
     "kron2-f16-n12": dict(kind=2, n=12, batch=1 << 20, io="f16", compute="native", seed=4),
     "kron2-bf16x3-n8": dict(kind=2, n=8, batch=1 << 20, io="f32", compute="bf16x3", seed=4),
